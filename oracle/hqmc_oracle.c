@@ -1,0 +1,452 @@
+/*
+ * hqmc_oracle.c -- plain FP64 CPU oracle for the worldline FFBS + Hirsch-Gibbs sweep
+ * of arXiv 2510.13866 ("FFT-Accelerated Auxiliary Variable MCMC for Fermionic
+ * Lattice Models").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct statement of
+ * what the GPU path computes.  It is called only from tests/, from the smoke check
+ * and from the benchmark's CPU-baseline leg.  The product path never links, loads
+ * or calls it, and it shares no code, header or table generator with the CUDA
+ * library: every table below is computed here from its definition.
+ *
+ * Conventions (one line each; the readings of the paper are listed in the design doc):
+ *   site index      x = ix + L*iy on an L x L torus, N = L*L.
+ *   slices          l = 0..M-1, M = beta/dtau; a worldline closes: x_M == x_0 (Sec. 3.1).
+ *   propagator      g(d) = (1/L) sum_j exp(2 t dtau cos(2 pi j/L)) cos(2 pi j d/L),
+ *                   G(dx,dy) = g(dx) g(dy) = <x+d| exp(-dtau K) |x>, the
+ *                   real-space form of the kinetic factors D(k)D(k') of Eq. (Tkk)
+ *                   with eps_k = -2t sum_a cos k_a (Sec. 3.3).
+ *   slice potential W_{l,sigma}(x) = exp(sigma * lambda * s_{x l}), sigma=+1 (up), -1 (down),
+ *                   cosh(lambda) = exp(dtau U / 2)  (Hirsch transformation, Eq. hirsch).
+ *   target          pi(X, s) ~ prod_{sigma,p,l} W_{l sigma}(x_l) G(x_{l+1} - x_l), s uniform.
+ *   forward filter  alpha <- G * (W_l . alpha), Eq. (ffbsFwd) in the position basis.
+ *   backward draw   P(x_l | x_{l+1}) ~ f_l(x_l) G(x_{l+1} - x_l)   (Sec. 3.5.2).
+ *   Gibbs           P(s = +1 | paths) = (1 + tanh(lambda m)) / 2, m = n_up - n_dn (Sec. 3.5.4).
+ *   random numbers  Philox4x64-10 of Salmon, Moraes, Dror and Shaw (SC'11), key (seed, 0),
+ *                   counter (j >> 2, i, phase, sweep), output word j & 3, u = (w >> 11) 2^-53.
+ *                   phase 0: FFBS draw, i = sigma*Nsig + p, j = l
+ *                   phase 1: Gibbs draw, i = l, j = x
+ *                   phase 2: anchor slice, i = 0, j = 0
+ *                   phase 3: initial field, sweep = 2^64 - 1, i = l, j = x
+ *
+ * Every function that has no independent pin in tests/ says "parity unpinned" here;
+ * at present every function is pinned (see tests/test_oracle_*.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846264338327950288
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x64-10 (Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", */
+/* SC'11): ten rounds of a 64x64->128 multiply S-box with a Weyl key schedule.  */
+/* ------------------------------------------------------------------------- */
+static void orc_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        orc_mulhilo64(M0, c[0], &hi0, &lo0);
+        orc_mulhilo64(M1, c[2], &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* One uniform in [0,1) for stream (seed, sweep, phase, i, j). */
+double orc_uniform(uint64_t seed, uint64_t sweep, uint64_t phase, uint64_t i, uint64_t j)
+{
+    uint64_t ctr[4] = {j >> 2, i, phase, sweep}, key[2] = {seed, 0}, w[4];
+    orc_philox4x64_10(ctr, key, w);
+    return (double)(w[j & 3] >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model constants                                                            */
+/* ------------------------------------------------------------------------- */
+
+/* lambda with cosh(lambda) = exp(dtau U / 2) (Hirsch transformation, Eq. hirsch). */
+double orc_lambda(double U, double dtau)
+{
+    return acosh(exp(0.5 * dtau * U));
+}
+
+/* 1D propagator g(d) and its t-derivative, written out from the definition
+ * exp(-dtau K) with eps_k = -2t cos k (Sec. 3.3, item 1). */
+void orc_g_table(int L, double t, double dtau, double *g, double *dg)
+{
+    for (int d = 0; d < L; ++d) {
+        double s = 0.0, ds = 0.0;
+        for (int j = 0; j < L; ++j) {
+            double ck = cos(2.0 * ORC_PI * j / L);
+            double e = exp(2.0 * t * dtau * ck);
+            double ph = cos(2.0 * ORC_PI * (double)j * (double)d / L);
+            s += e * ph;
+            ds += 2.0 * dtau * ck * e * ph;
+        }
+        g[d] = s / L;
+        if (dg) dg[d] = ds / L;
+    }
+}
+
+static inline int orc_wrap(int v, int L) { v %= L; return v < 0 ? v + L : v; }
+
+/* G(y - x) for sites x, y. */
+static inline double orc_G(const double *g, int L, int x, int y)
+{
+    int dx = orc_wrap((y % L) - (x % L), L), dy = orc_wrap((y / L) - (x / L), L);
+    return g[dx] * g[dy];
+}
+
+/* dG/dt(y - x) = g'(dx) g(dy) + g(dx) g'(dy). */
+static inline double orc_dG(const double *g, const double *dg, int L, int x, int y)
+{
+    int dx = orc_wrap((y % L) - (x % L), L), dy = orc_wrap((y / L) - (x / L), L);
+    return dg[dx] * g[dy] + g[dx] * dg[dy];
+}
+
+/* out(y) = sum_x K(y - x) in(x): direct periodic convolution, O(N^2). */
+static void orc_conv(int L, const double *g, const double *in, double *out)
+{
+    int N = L * L;
+    for (int y = 0; y < N; ++y) {
+        double acc = 0.0;
+        for (int x = 0; x < N; ++x) acc += orc_G(g, L, x, y) * in[x];
+        out[y] = acc;
+    }
+}
+
+static void orc_conv_dG(int L, const double *g, const double *dg, const double *in, double *out)
+{
+    int N = L * L;
+    for (int y = 0; y < N; ++y) {
+        double acc = 0.0;
+        for (int x = 0; x < N; ++x) acc += orc_dG(g, dg, L, x, y) * in[x];
+        out[y] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initial state                                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Site of worldline p of spin sigma at the start: up particles fill sublattice A
+ * ((ix+iy) even) in row-major order, then sublattice B; down particles fill B then A. */
+int orc_initial_site(int L, int sigma, int p)
+{
+    int N = L * L, k = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int want = (sigma == 0) ? pass : 1 - pass; /* parity class to take in this pass */
+        for (int x = 0; x < N; ++x) {
+            if (((x % L) + (x / L)) % 2 != want) continue;
+            if (k == p) return x;
+            ++k;
+        }
+    }
+    return -1;
+}
+
+/* s[l*N + x] = +-1 from phase 3; x[((sigma*Nsig)+p)*M + l] = static worldline. */
+void orc_init_state(int L, int M, int Nsig, uint64_t seed, int8_t *s, int32_t *xpath)
+{
+    int N = L * L;
+    for (int l = 0; l < M; ++l)
+        for (int x = 0; x < N; ++x)
+            s[l * N + x] = orc_uniform(seed, UINT64_MAX, 3, (uint64_t)l, (uint64_t)x) < 0.5 ? 1 : -1;
+    for (int sg = 0; sg < 2; ++sg)
+        for (int p = 0; p < Nsig; ++p) {
+            int site = orc_initial_site(L, sg, p);
+            for (int l = 0; l < M; ++l) xpath[((size_t)sg * Nsig + p) * M + l] = site;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Forward filter and backward sampling (Sec. 3.5.2, Eq. ffbsFwd)             */
+/* ------------------------------------------------------------------------- */
+
+/* Forward filter of one worldline anchored at slice a, site xa.
+ * W is [M][N] (slice potential of this spin).  If f_store is non-NULL it receives
+ * f_l = W_l . alpha_l (sum-normalised alpha) for every slice l.
+ * Returns log Z = log sum over closed paths with x_a held of prod W G. */
+double orc_filter(int L, int M, const double *g, const double *W, int a, int xa, double *f_store)
+{
+    int N = L * L;
+    double *alpha = calloc(N, sizeof(double)), *f = malloc(N * sizeof(double)),
+           *nxt = malloc(N * sizeof(double));
+    double logZ = 0.0;
+    alpha[xa] = 1.0;
+    for (int i = 0; i < M; ++i) {
+        int l = (a + i) % M;
+        for (int x = 0; x < N; ++x) f[x] = W[(size_t)l * N + x] * alpha[x];
+        if (f_store) memcpy(f_store + (size_t)l * N, f, N * sizeof(double));
+        orc_conv(L, g, f, nxt);
+        double c = 0.0;
+        for (int x = 0; x < N; ++x) c += nxt[x];
+        for (int x = 0; x < N; ++x) alpha[x] = nxt[x] / c;
+        logZ += log(c);
+    }
+    logZ += log(alpha[xa]);
+    free(alpha); free(f); free(nxt);
+    return logZ;
+}
+
+/* Backward sampling of one worldline given the stored f_l: for i = M-1..1,
+ * l = (a+i) mod M, draw x_l from p(y) ~ f_l(y) G(x_{l+1} - y) by the row-major
+ * inverse CDF: the smallest y with u*S < C(y).  margin[l] (optional) receives the
+ * distance from u*S to the nearer edge of the chosen CDF interval, over S. */
+void orc_backward(int L, int M, const double *g, const double *f_store, int a,
+                  uint64_t seed, uint64_t sweep, uint64_t wl, int32_t *xpath, double *margin)
+{
+    int N = L * L;
+    double *p = malloc(N * sizeof(double));
+    for (int i = M - 1; i >= 1; --i) {
+        int l = (a + i) % M, next = xpath[(l + 1) % M];
+        double S = 0.0;
+        for (int y = 0; y < N; ++y) {
+            p[y] = f_store[(size_t)l * N + y] * orc_G(g, L, y, next);
+            S += p[y];
+        }
+        double u = orc_uniform(seed, sweep, 0, wl, (uint64_t)l);
+        double target = u * S, C = 0.0, Cprev = 0.0;
+        int pick = -1;
+        for (int y = 0; y < N; ++y) {
+            Cprev = C;
+            C += p[y];
+            if (target < C) { pick = y; break; }
+        }
+        if (pick < 0) { pick = next; Cprev = C = target; } /* S == 0: degenerate, stay */
+        xpath[l] = pick;
+        if (margin) {
+            double m1 = target - Cprev, m2 = C - target;
+            margin[l] = (S > 0.0) ? (m1 < m2 ? m1 : m2) / S : 0.0;
+        }
+    }
+    if (margin) margin[a] = INFINITY; /* the anchor is held, not drawn */
+    free(p);
+}
+
+/* ------------------------------------------------------------------------- */
+/* One sweep of one chain: anchor, FFBS of every worldline, occupancy, Gibbs.  */
+/* ------------------------------------------------------------------------- */
+
+/* Inputs/outputs:
+ *   s      [M][N] int8 +-1, updated by the Gibbs step.
+ *   xpath  [2][Nsig][M] int32 site indices, updated by FFBS.
+ *   logw   [2][Nsig] filter log-weights computed with the field before Gibbs (nullable).
+ *   hist   [2][M][N] int32 occupancy of the new paths (nullable).
+ *   margin [2][Nsig][M] CDF margins of every draw (nullable).
+ *   links  [2][Nsig] sum over the M links of d/dt log G(x_{l+1} - x_l) (nullable).
+ *   anchor receives the anchor slice (nullable).
+ *   nwl_limit: if >= 0, only the first nwl_limit worldlines of each spin are
+ *   resampled (a bounded sample for timing); the Gibbs step is then skipped.
+ * Worldlines are independent given s, so they are processed in parallel. */
+int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
+              int8_t *s, int32_t *xpath, double *logw, int32_t *hist, double *margin,
+              double *links, int *anchor, int nwl_limit)
+{
+    int N = L * L;
+    double lam = orc_lambda(U, dtau);
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    int a = (int)floor(orc_uniform(seed, sweep, 2, 0, 0) * M);
+    if (a >= M) a = M - 1;
+    if (anchor) *anchor = a;
+    double *W = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg) {
+        double sigma = sg == 0 ? 1.0 : -1.0;
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x)
+                W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
+    }
+    int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
+    int total = 2 * nwl;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < total; ++k) {
+        int sg = k / nwl, p = k % nwl;
+        uint64_t wl = (uint64_t)sg * Nsig + p;
+        int32_t *xp = xpath + wl * M;
+        double *fst = malloc((size_t)M * N * sizeof(double));
+        double lz = orc_filter(L, M, g, W + (size_t)sg * M * N, a, xp[a], fst);
+        if (logw) logw[wl] = lz;
+        orc_backward(L, M, g, fst, a, seed, sweep, wl, xp, margin ? margin + wl * M : NULL);
+        if (links) {
+            double acc = 0.0;
+            for (int l = 0; l < M; ++l) {
+                int x0 = xp[l], x1 = xp[(l + 1) % M];
+                int dx = orc_wrap((x1 % L) - (x0 % L), L), dy = orc_wrap((x1 / L) - (x0 / L), L);
+                acc += dg[dx] / g[dx] + dg[dy] / g[dy];
+            }
+            links[wl] = acc;
+        }
+        free(fst);
+    }
+    if (nwl_limit < 0 || nwl_limit >= Nsig) {
+        int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
+        memset(n, 0, (size_t)2 * M * N * sizeof(int32_t));
+        for (int sg = 0; sg < 2; ++sg)
+            for (int p = 0; p < Nsig; ++p)
+                for (int l = 0; l < M; ++l)
+                    n[((size_t)sg * M + l) * N + xpath[((size_t)sg * Nsig + p) * M + l]] += 1;
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x) {
+                int m = n[(size_t)l * N + x] - n[((size_t)M + l) * N + x];
+                double pplus = 1.0 / (1.0 + exp(-2.0 * lam * m));
+                double u = orc_uniform(seed, sweep, 1, (uint64_t)l, (uint64_t)x);
+                s[(size_t)l * N + x] = (u < pplus) ? 1 : -1;
+            }
+        if (!hist) free(n);
+    }
+    free(g); free(dg); free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Forward-backward marginals and d log Z / dt of one worldline (adjoint of   */
+/* Eq. ffbsFwd).  Anchor slice 0, site x0.  v is [M][N] log-potential.         */
+/* ------------------------------------------------------------------------- */
+double orc_marginals(int L, int M, const double *g, const double *dg, const double *v, int x0,
+                     double *marg, double *dlogZ_dt)
+{
+    int N = L * L;
+    double *F = malloc((size_t)M * N * sizeof(double));
+    double *alpha = calloc(N, sizeof(double)), *tmp = malloc(N * sizeof(double));
+    double *b = calloc(N, sizeof(double)), *H = malloc(N * sizeof(double)),
+           *Hd = malloc(N * sizeof(double));
+    double logZ = 0.0;
+    alpha[x0] = 1.0;
+    for (int l = 0; l < M; ++l) {
+        for (int x = 0; x < N; ++x) F[(size_t)l * N + x] = exp(v[(size_t)l * N + x]) * alpha[x];
+        orc_conv(L, g, F + (size_t)l * N, tmp);
+        double c = 0.0;
+        for (int x = 0; x < N; ++x) c += tmp[x];
+        for (int x = 0; x < N; ++x) alpha[x] = tmp[x] / c;
+        logZ += log(c);
+    }
+    logZ += log(alpha[x0]);
+    /* backward messages: b_M = delta_{x0}; H_l = G * b_{l+1}; b_l = W_l H_l */
+    b[x0] = 1.0;
+    double dt = 0.0;
+    for (int l = M - 1; l >= 0; --l) {
+        orc_conv(L, g, b, H);       /* G is even, so correlation == convolution */
+        orc_conv_dG(L, g, dg, b, Hd);
+        double z = 0.0, zd = 0.0;
+        for (int x = 0; x < N; ++x) {
+            z += F[(size_t)l * N + x] * H[x];
+            zd += F[(size_t)l * N + x] * Hd[x];
+        }
+        if (marg)
+            for (int x = 0; x < N; ++x) marg[(size_t)l * N + x] = F[(size_t)l * N + x] * H[x] / z;
+        dt += zd / z;
+        double c = 0.0;
+        for (int x = 0; x < N; ++x) { b[x] = exp(v[(size_t)l * N + x]) * H[x]; c += b[x]; }
+        for (int x = 0; x < N; ++x) b[x] /= c;
+    }
+    if (dlogZ_dt) *dlogZ_dt = dt;
+    free(F); free(alpha); free(tmp); free(b); free(H); free(Hd);
+    return logZ;
+}
+
+/* Whole-chain gradient: logZ = sum over worldlines, each anchored at slice 0 on
+ * its current site; dv[sigma][l][x] = sum_p marginal; v defaults to sigma*lambda*s. */
+double orc_chain_grad(int L, int M, int Nsig, double t, double U, double dtau, const int8_t *s,
+                      const double *v_in, const int32_t *xpath, double *dv, double *dlogZ_dt)
+{
+    int N = L * L;
+    double lam = orc_lambda(U, dtau);
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    double *v = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg)
+        for (size_t k = 0; k < (size_t)M * N; ++k)
+            v[(size_t)sg * M * N + k] = v_in ? v_in[(size_t)sg * M * N + k]
+                                             : (sg == 0 ? 1.0 : -1.0) * lam * s[k];
+    if (dv) memset(dv, 0, (size_t)2 * M * N * sizeof(double));
+    double total = 0.0, dtt = 0.0;
+    int nw = 2 * Nsig;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total, dtt)
+    for (int k = 0; k < nw; ++k) {
+        int sg = k / Nsig;
+        double *marg = malloc((size_t)M * N * sizeof(double)), d = 0.0;
+        total += orc_marginals(L, M, g, dg, v + (size_t)sg * M * N, xpath[(size_t)k * M], marg, &d);
+        dtt += d;
+        if (dv) {
+#pragma omp critical
+            for (size_t q = 0; q < (size_t)M * N; ++q) dv[(size_t)sg * M * N + q] += marg[q];
+        }
+        free(marg);
+    }
+    if (dlogZ_dt) *dlogZ_dt = dtt;
+    free(g); free(dg); free(v);
+    return total;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Observables of one configuration (Sec. 4, "Observables"), summed over       */
+/* slices.  hist is [2][M][N]; out receives                                    */
+/*   out[0] = sum n_up + n_dn, out[1] = sum n_up n_dn, out[2] = sum m^2        */
+/* and Sk[k] = sum_l |m^(k)|^2 / N with m^(k) = sum_x m(x) e^{-i k.x},          */
+/* Cr[r] = sum_l sum_x m(x) m(x + r) / N, both on the N-point grid.            */
+/* ------------------------------------------------------------------------- */
+void orc_measure(int L, int M, const int32_t *hist, double *out, double *Sk, double *Cr)
+{
+    int N = L * L;
+    double sn = 0, sd = 0, sm = 0;
+    int *m = malloc(N * sizeof(int));
+    if (Sk) memset(Sk, 0, N * sizeof(double));
+    if (Cr) memset(Cr, 0, N * sizeof(double));
+    for (int l = 0; l < M; ++l) {
+        for (int x = 0; x < N; ++x) {
+            int nu = hist[(size_t)l * N + x], nd = hist[((size_t)M + l) * N + x];
+            sn += nu + nd; sd += (double)nu * nd;
+            m[x] = nu - nd; sm += (double)m[x] * m[x];
+        }
+        if (Sk)
+            for (int k = 0; k < N; ++k) {
+                int kx = k % L, ky = k / L;
+                double re = 0.0, im = 0.0;
+                for (int x = 0; x < N; ++x) {
+                    double ph = -2.0 * ORC_PI * ((double)kx * (x % L) + (double)ky * (x / L)) / L;
+                    re += m[x] * cos(ph); im += m[x] * sin(ph);
+                }
+                Sk[k] += (re * re + im * im) / N;
+            }
+        if (Cr)
+            for (int r = 0; r < N; ++r) {
+                int rx = r % L, ry = r / L;
+                double acc = 0.0;
+                for (int x = 0; x < N; ++x) {
+                    int y = orc_wrap(x % L + rx, L) + L * orc_wrap(x / L + ry, L);
+                    acc += (double)m[x] * m[y];
+                }
+                Cr[r] += acc / N;
+            }
+    }
+    out[0] = sn; out[1] = sd; out[2] = sm;
+    free(m);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
