@@ -1,0 +1,285 @@
+#!/usr/bin/env python
+"""Sweeps/s of the worldline FFBS + Hirsch-Gibbs sweep on synthetic Hubbard lattices.
+
+Workload (one step = one sweep of the whole batch: anchor draw, FFBS of every
+worldline, Gibbs resample of every field, observable accumulation):
+  L=32 (N=1024), t=1, U=4, beta=4, dtau=0.05 (M=80), half filling (512 up + 512 down
+  worldlines), 64 independent chains with Philox seeds 0..63 (offset 64*rank per rank),
+  batched FP32 filter with FP64 log-normaliser, one CUDA-graph replay per sweep.
+
+Printed beside it on the same JSON line: the FFBS kernel's roofline from CUDA events
+taken live around its launches, the plain FP64 form (same kernels in double, one launch
+per phase, no graph), the end-to-end rate through the public API with host buffers,
+and the CPU oracle timed on a bounded sample on this host's cores.
+
+--impl reference times the CPU oracle (the test oracle of this repository, FP64) on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORK = dict(L=32, t=1.0, U=4.0, beta=4.0, dtau=0.05, filling=1.0, chains=64)
+METRIC = "sweeps/s at L=32 (batched FP32 vs plain FP64 GPU, same accuracy); % HBM roofline"
+WORKLOAD = ("2D Hubbard L=32 (N=1024) t=1 U=4 beta=4 dtau=0.05 (M=80) half filling, "
+            "512+512 worldlines x 64 chains, Philox seeds 0..63; FP32 FFT filter, FP64 log Z")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+def start_clocks(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def stop_clocks(proc, f, path, device):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(device):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(target_s=12.0):
+    """Time the FP64 oracle (OpenMP over worldlines) on the first k worldlines of each
+    spin of chain 0 for one sweep; extrapolate to the whole 64-chain batch."""
+    import oracle
+
+    w = WORK
+    orc = oracle.Chain(w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
+    cores = oracle.num_threads()
+    k = max(1, cores // 2)
+    t0 = time.perf_counter()
+    orc.sweep(nwl_limit=k)
+    dt = time.perf_counter() - t0
+    k2 = max(k, min(orc.Nsig, int(k * target_s / max(dt, 1e-3))))
+    k2 = (k2 + cores - 1) // cores * cores // 2 or k
+    orc2 = oracle.Chain(w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
+    t0 = time.perf_counter()
+    orc2.sweep(nwl_limit=k2)
+    dt2 = time.perf_counter() - t0
+    per_wl = dt2 / (2 * k2)
+    total_wl = w["chains"] * 2 * orc2.Nsig
+    return {"value": 1.0 / (per_wl * total_wl), "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+            "sample": f"chain 0, first {k2} worldlines of each spin, 1 sweep ({dt2:.1f} s), "
+                      f"extrapolated per worldline to {total_wl} worldlines"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    w = WORK
+    cores = oracle.num_threads()
+    # one step = one sweep of a bounded sample (k worldlines per spin of chain 0)
+    orc = oracle.Chain(w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
+    t0 = time.perf_counter()
+    orc.sweep(nwl_limit=1)
+    one = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    k = max(1, min(orc.Nsig, int(budget / max(one, 1e-3) / 2)))
+    for _ in range(args.warmup):
+        orc.sweep(nwl_limit=k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.sweep(nwl_limit=k)
+        times.append(time.perf_counter() - t0)
+    per_wl = sum(times) / (len(times) * 2 * k)
+    total_wl = w["chains"] * 2 * orc.Nsig
+    value = 1.0 / (per_wl * total_wl)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_worldlines_per_spin": k},
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: chain 0, first {k} worldlines of each spin, one sweep; "
+                                       f"extrapolated to {total_wl} worldlines"},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2510_13866_gb300 import Lattice
+
+    w = WORK
+    seeds = [rank * w["chains"] + c for c in range(w["chains"])]
+    lat = Lattice(w["L"], seeds, precision="fp32", device=local)
+    lat.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
+    lat.prepare()
+    L, M, Ns = lat.shapes[0]
+    stream = torch.cuda.current_stream(local)
+    lat.sweep(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"hqmc_clocks_{os.getpid()}.csv")
+    proc, fh = start_clocks(clk_path)
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.sweep(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = stop_clocks(proc, fh, clk_path, local)
+    barrier()
+    ms = max_over_ranks(ms)
+    value = world * args.steps / (ms / 1e3)
+
+    # FFBS kernel time from events around its launches (same K sweeps, no graph)
+    lat.set_profiling(args.steps)
+    lat.sweep(args.steps)
+    ffbs_ms, slice_ms, nprof = lat.profile_read()
+    lat.set_profiling(0)
+    ffbs_avg = ffbs_ms / max(1, nprof)
+    slice_avg = slice_ms / max(1, nprof)
+    part_slices = w["chains"] * 2 * Ns * M
+    alg_bytes = part_slices * 8.0 * L * L          # f_l written (4N B) and read back (4N B)
+    alg_flops = part_slices * (5.0 * L * L * np.log2(L * L) + 4.0 * L * L)
+    hbm_peak, peak_src, sm_max = peaks()
+    achieved = alg_bytes / (ffbs_avg / 1e3) / 1e9
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+    achieved_flops = alg_flops / (ffbs_avg / 1e3) / 1e12
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "ffbs_traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": "ffbs_kernel<float,32>", "kernel_ms": ffbs_avg, "gibbs_measure_ms": slice_avg,
+                "alu": {"achieved_tflops": achieved_flops, "peak_tflops": alu_peak,
+                        "frac": achieved_flops / alu_peak}}
+
+    # end to end through the public API: host log-weight buffer every step
+    ke = min(args.steps, 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        lat.sweep(1, logw=True)
+    te = time.perf_counter() - t0
+    e2e_val = max_over_ranks(te)
+    e2e = {"value": world * ke / e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": int(8 * w["chains"] * 2 * Ns) + 4}
+    lat.close()
+
+    # plain FP64 form: same kernels in double, one launch per phase, no graph
+    fp64 = None
+    if args.fp64_steps > 0:
+        lat64 = Lattice(w["L"], seeds, precision="fp64", device=local)
+        lat64.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
+        lat64.sweep(1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat64.sweep(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        v64 = world * args.fp64_steps / (ms64 / 1e3)
+        fp64 = {"value": v64, "unit": "sweeps/s", "steps": args.fp64_steps, "fp32_over_fp64": value / v64}
+        lat64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "L": L, "M": M, "chains_per_gpu": w["chains"],
+                           "worldlines_per_chain": 2 * Ns, "parallelism": f"chains sharded over {world} GPU(s)",
+                           "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2"},
+                "particle_slice_updates_per_s": value * part_slices,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * 3, "clocks": clocks, "fp64_plain": fp64}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

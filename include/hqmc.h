@@ -1,0 +1,181 @@
+/*
+ * hqmc.h -- C ABI of the GB300 (sm_103a) worldline sampler for the 2D repulsive
+ * Hubbard model of arXiv 2510.13866, "FFT-Accelerated Auxiliary Variable MCMC for
+ * Fermionic Lattice Models".
+ *
+ * One sweep of a chain is
+ *   1. an anchor slice a drawn per chain,
+ *   2. forward-filtering backward-sampling (FFBS) of every worldline with its
+ *      position at slice a held (Sec. 3.5.2, Eq. ffbsFwd and the backward
+ *      conditional that follows it),
+ *   3. the factorised Gibbs resample of every Hirsch field s_{x,l}
+ *      (Sec. 3.5.4: P(s=+1 | paths) = (1 + tanh(lambda m)) / 2, m = n_up - n_dn),
+ *   4. accumulation of the observables of Sec. 4 from the new occupations.
+ *
+ * Conventions used by every entry point:
+ *   - site x = ix + L*iy on an L x L torus, N = L*L; slices l = 0..M-1, M = beta/dtau.
+ *   - the forward filter runs in the position basis: alpha <- G * (W_l . alpha)
+ *     with G(d) = <x+d| exp(-dtau K) |x> (the kinetic factors D(k) of Eq. Tkk,
+ *     eps_k = -2t (cos kx + cos ky)) and W_{l,sigma}(x) = exp(sigma lambda s_{x,l}),
+ *     sigma = +1 for up, -1 for down, cosh(lambda) = exp(dtau U / 2) (Eq. hirsch).
+ *   - worldlines close on themselves (permutation = identity); log-weights leave out
+ *     every constant of the Hirsch identity and the field prior 2^{-NM}.
+ *   - random numbers: Philox4x64-10 (Salmon et al., SC'11), key (seed, 0),
+ *     counter (j >> 2, i, phase, sweep), word j & 3, u = (word >> 11) * 2^-53;
+ *     phase 0 = FFBS draw (i = sigma*Nsig + p, j = l), 1 = Gibbs (i = l, j = x),
+ *     2 = anchor (i = j = 0), 3 = initial field (sweep = 2^64-1, i = l, j = x).
+ *   - "packed over chains" means chain 0's block, then chain 1's, ... with no padding.
+ *
+ * Errors: every int-returning call returns HQMC_OK (0) or a negative HQMC_ERR_* code;
+ * hqmc_strerror gives its text and hqmc_last_error_detail the context's last message.
+ * A context is bound to one device and one CUDA stream; it is not thread safe.
+ */
+#ifndef HQMC_H
+#define HQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hqmc_ctx hqmc_ctx;
+
+/* arithmetic of the forward filter and backward sampler */
+#define HQMC_FP32 0 /* FP32 FFT and convolution; FP64 only for log Z and the Gibbs ratios */
+#define HQMC_FP64 1 /* every step in FP64 (the plain comparison form) */
+
+#define HQMC_OK 0
+#define HQMC_ERR_ARG (-1)         /* invalid argument (see each call) */
+#define HQMC_ERR_NOMEM (-2)       /* device allocation failed or workspace too small */
+#define HQMC_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define HQMC_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired */
+#define HQMC_ERR_STATE (-5)       /* call out of order (e.g. sweep before set_params) */
+#define HQMC_ERR_UNSUPPORTED (-6) /* lattice size or mode not built into this library */
+#define HQMC_ERR_NUMERIC (-7)     /* a draw met an all-zero CDF or log Z met a non-positive amplitude */
+
+/* Observables of one chain, averaged over slices and over the sweeps accumulated
+ * since the last reset (Sec. 4, "Observables").  Per-site quantities. */
+typedef struct {
+    int64_t n_samples; /* sweeps accumulated */
+    double density;    /* <n_up + n_dn> */
+    double double_occ; /* D = <n_up n_dn> */
+    double m2;         /* <(n_up - n_dn)^2> = 4 <(S^z)^2> */
+    double ekin;       /* -(t/beta) <sum over links d/dt log G(x_{l+1} - x_l)> / N */
+    double s_pipi;     /* S(k) at k = (pi, pi) (nearest grid point for odd L) */
+} hqmc_obs;
+
+/* Create a context for n_chains independent chains on CUDA device `device`.
+ *   L[c]      linear size of chain c's lattice; 2 <= L[c] and L[c] must be one of the
+ *             sizes built into the library (hqmc_supported_L), else HQMC_ERR_UNSUPPORTED.
+ *   seeds[c]  Philox key of chain c.
+ *   precision HQMC_FP32 or HQMC_FP64.
+ * *out receives the context (caller frees it with hqmc_destroy).  No device memory is
+ * allocated here.  Errors: HQMC_ERR_ARG (null pointers, n_chains < 1, bad precision),
+ * HQMC_ERR_UNSUPPORTED, HQMC_ERR_CUDA (device cannot be selected). */
+int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t *seeds,
+                      int precision, int device);
+
+/* Model parameters of chain `chain` (-1 = all chains): hopping t >= 0, U >= 0,
+ * inverse temperature beta and slice dtau with beta/dtau an integer M (within 1e-9),
+ * filling with filling*N/2 a positive integer Nsig (worldlines per spin, 2 Nsig <= 2N).
+ * U < 0 (the Gaussian transformation of Sec. 3.5.5) is rejected.
+ * Before the first sweep any parameter may change; afterwards only t and U may change
+ * (M and Nsig fix the state's shape), else HQMC_ERR_STATE.  Errors: HQMC_ERR_ARG. */
+int hqmc_set_params(hqmc_ctx *ctx, int chain, double t, double U, double beta, double dtau,
+                    double filling);
+
+/* CUDA stream (a cudaStream_t passed as void*) on which every later call is ordered;
+ * NULL = the legacy default stream.  Changing it drops the captured sweep graph. */
+int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
+
+/* Launch configuration: use_graph = replay one captured CUDA graph per sweep;
+ * persistent = size the FFBS grid to the resident capacity (each worldline group
+ * loops over pairs) instead of one group per pair; warps_per_cta in {1,2,4,8,16}
+ * (0 = default).  Takes effect at the next sweep.  Errors: HQMC_ERR_ARG. */
+int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
+
+/* Device memory the context needs (state + scratch), in bytes, for the current
+ * parameters and launch configuration.  Errors: HQMC_ERR_STATE before set_params. */
+int hqmc_workspace_size(hqmc_ctx *ctx, size_t *bytes);
+
+/* Hand the context a caller-owned device buffer of at least hqmc_workspace_size bytes,
+ * 256-byte aligned; the caller keeps it alive until hqmc_destroy or the next attach.
+ * Without an attached buffer the context allocates its own with cudaMalloc at the
+ * first sweep.  Attaching re-initialises the chain state (fields and worldlines).
+ * Errors: HQMC_ERR_ARG (null, misaligned), HQMC_ERR_NOMEM (too small). */
+int hqmc_attach_workspace(hqmc_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Run n_sweeps >= 0 sweeps on the context's stream.  logw_out (nullable, host) receives
+ * the FP64 filter log-weights log Z_p of the LAST sweep, packed over chains as
+ * [2][Nsig] (spin-major), where Z_p = sum over closed paths of worldline p with its
+ * anchor-slice position held of prod_l W_l(x_l) G(x_{l+1} - x_l), evaluated with the
+ * field before that sweep's Gibbs step.  The call blocks until the sweeps finish.
+ * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
+int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
+
+/* Read the accumulated observables.  out: host array [n_chains] (nullable).
+ * Sk, Cr (nullable, host) receive per chain the spin structure factor
+ * S(k) = (1/N) sum_{ij} e^{ik(r_i-r_j)} <S^z_i S^z_j> on the N-point grid k = kx + L ky
+ * (k_a = 2 pi k_a / L) and C(r) = <S^z_0 S^z_r> at r = rx + L ry, packed over chains.
+ * reset != 0 zeroes the accumulators after reading.  Errors: HQMC_ERR_STATE, _CUDA. */
+int hqmc_measure(hqmc_ctx *ctx, hqmc_obs *out, double *Sk, double *Cr, int reset);
+
+/* Log-weight of the current worldlines with every worldline anchored at slice 0 on its
+ * current site, and its gradient (the adjoint of the forward filter of Eq. ffbsFwd):
+ *   logZ[c]      = sum_{sigma,p} log Z_p                                      (host [n_chains])
+ *   dlogZ_dv     = d logZ / d v_{l,sigma}(x), v = log W, i.e. the summed
+ *                  forward-backward site marginals, device [2][M][N] per chain packed
+ *                  over chains, element type float (FP32 context) or double (FP64)
+ *   dlogZ_dt[c]  = d logZ / d t                                              (host [n_chains])
+ * v (nullable, device, same type and layout as dlogZ_dv) replaces log W = sigma lambda s.
+ * Any output pointer may be NULL.  The FP32 context checkpoints alpha every ceil(sqrt M)
+ * slices in BF16 with a per-slice exponent and recomputes in between.
+ * Errors: HQMC_ERR_STATE, HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
+int hqmc_log_weight_grad(hqmc_ctx *ctx, const void *v, double *logZ, void *dlogZ_dv,
+                         double *dlogZ_dt);
+
+/* Shape of chain c: L, M (slices), Nsig (worldlines per spin).  Errors: HQMC_ERR_ARG. */
+int hqmc_chain_shape(hqmc_ctx *ctx, int chain, int *L, int *M, int *Nsig);
+
+/* Copy chain c's state to host buffers (each nullable):
+ *   s [M][N] int8 (+1/-1), x [2][Nsig][M] int32 sites, anchor = last anchor slice
+ *   (-1 before the first sweep), sweeps = sweeps done.  Errors: HQMC_ERR_STATE, _CUDA. */
+int hqmc_get_state(hqmc_ctx *ctx, int chain, int8_t *s, int32_t *x, int *anchor,
+                   uint64_t *sweeps);
+
+/* Overwrite chain c's field and worldlines (layouts as in hqmc_get_state; sites must be
+ * in [0, N), s in {-1, +1}); sweeps (if non-NULL) sets the sweep counter of the whole
+ * context (used for checkpoint/resume: a restored context reproduces the draws).
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_STATE, HQMC_ERR_CUDA. */
+int hqmc_set_state(hqmc_ctx *ctx, int chain, const int8_t *s, const int32_t *x,
+                   const uint64_t *sweeps);
+
+/* Per-phase device timing.  max_sweeps > 0 turns it on: later sweeps launch without
+ * a graph and record CUDA events around the FFBS launches (on the streams they run on)
+ * and around the Gibbs/measure kernel, for up to max_sweeps sweeps; 0 turns it off.
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_CUDA. */
+int hqmc_set_profiling(hqmc_ctx *ctx, int max_sweeps);
+
+/* Sum over the recorded sweeps of the FFBS and the Gibbs/measure device times (ms)
+ * and the number of sweeps recorded; clears the record.  Errors: HQMC_ERR_STATE, _CUDA. */
+int hqmc_profile_read(hqmc_ctx *ctx, double *ffbs_ms, double *slice_ms, int *n_sweeps);
+
+/* Lattice sizes built into this library: writes up to cap entries, returns the count. */
+int hqmc_supported_L(int *out, int cap);
+
+/* Release the context and any memory it allocated itself (not an attached workspace). */
+void hqmc_destroy(hqmc_ctx *ctx);
+
+/* Static text for an HQMC_* code. */
+const char *hqmc_strerror(int code);
+
+/* Last error message recorded on this context ("" if none); valid until the next call. */
+const char *hqmc_last_error_detail(hqmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HQMC_H */

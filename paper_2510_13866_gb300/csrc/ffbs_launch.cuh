@@ -1,0 +1,64 @@
+// ffbs_launch.cuh -- per-precision launch helpers of the FFBS kernel (included once
+// by ffbs_f32.cu and once by ffbs_f64.cu so the two precisions compile in parallel).
+#pragma once
+
+#include "ffbs.cuh"
+
+namespace hqmc {
+
+#define HQMC_FFBS_SIZES(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32)
+
+// launch only: the shared-memory attribute is set beforehand by ffbs_occ (never
+// during stream capture)
+template <typename T, int L>
+static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s) {
+    const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
+    ffbs_kernel<T, L><<<grid, wpc * 32, sm, s>>>(st, fl);
+    return cudaGetLastError();
+}
+
+// sets the kernel's dynamic shared-memory limit and reports resident CTAs per SM
+template <typename T, int L>
+static cudaError_t ffbs_occ(int wpc, int *blocks) {
+    const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
+    auto k = ffbs_kernel<T, L>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, wpc * 32, sm);
+}
+
+template <typename T>
+static cudaError_t ffbs_dispatch(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc,
+                                 cudaStream_t s) {
+    switch (L) {
+#define HQMC_CASE(n) \
+    case n: return ffbs_go<T, n>(st, fl, grid, wpc, s);
+        HQMC_FFBS_SIZES(HQMC_CASE)
+#undef HQMC_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static cudaError_t ffbs_occ_dispatch(int L, int wpc, int *blocks) {
+    switch (L) {
+#define HQMC_CASE(n) \
+    case n: return ffbs_occ<T, n>(wpc, blocks);
+        HQMC_FFBS_SIZES(HQMC_CASE)
+#undef HQMC_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static size_t ffbs_smem_dispatch(int L, int wpc) {
+    switch (L) {
+#define HQMC_CASE(n) \
+    case n: return ffbs_smem_bytes_t<T, n>(wpc);
+        HQMC_FFBS_SIZES(HQMC_CASE)
+#undef HQMC_CASE
+        default: return 0;
+    }
+}
+
+}  // namespace hqmc

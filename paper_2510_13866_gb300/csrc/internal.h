@@ -1,0 +1,99 @@
+// internal.h -- device-side data layout shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hqmc {
+
+constexpr int kMaxL = 128;
+constexpr int kPTab = 64;  // P(s=+1 | m) tabulated for |m| <= kPTab, computed beyond
+
+// Per-chain tables, computed on the host in FP64 at set_params.
+struct ChainTab {
+    double ghat_d[kMaxL];  // e^{2 t dtau cos(2 pi k / L)} / L          (1D kernel in k-space)
+    double g_d[kMaxL];     // g(d) = <x+d| e^{dtau t A} |x> in 1D        (real-space kernel)
+    double h_d[kMaxL];     // d/dt log g(d)
+    float ghat_f[kMaxL];
+    float g_f[kMaxL];
+    float h_f[kMaxL];
+    double dghat_d[kMaxL]; // d/dt ghat(k)
+    float dghat_f[kMaxL];
+    double pplus[2 * kPTab + 1];  // 1 / (1 + e^{-2 lambda m}), m = -kPTab..kPTab
+};
+
+// Per-chain shape, parameters and offsets into the context's device arrays.
+struct ChainDev {
+    int L, N, M, Nsig;
+    int npair;  // pairs per spin = ceil(Nsig / 2)
+    int wpl;    // 32-bit words per lattice line of the bit-packed field
+    uint64_t seed;
+    double lam;       // Hirsch lambda
+    double w_plus[2]; // W for s = +1, spin up / down: e^{+lambda}, e^{-lambda}
+    double w_minus[2];
+    double t, beta;
+    long long s_off;    // word offset of the field: rows [M][L][wpl] then cols [M][L][wpl]
+    long long x_off;    // int16 offset of worldlines [2][Nsig][M]
+    long long h_off;    // int32 offset of the occupancy histogram [2][M][N]
+    long long logw_off; // double offset of log-weights [2][Nsig]
+    long long v_off;    // element offset of [2][M][N] gradient arrays
+    long long meas_off; // offset into the measurement arrays (N per chain)
+};
+
+// Per-chain measurement accumulators (device, zeroed at reset).
+struct MeasAcc {
+    unsigned long long n_sum;   // sum over slices, sites of n_up + n_dn
+    unsigned long long d_sum;   // sum n_up n_dn
+    unsigned long long m2_sum;  // sum m^2
+    unsigned long long samples; // sweeps accumulated
+    double link_sum;            // sum over worldlines and links of d/dt log G
+    double pad[3];
+};
+
+struct DevState {
+    const ChainDev *chains;
+    const ChainTab *tabs;
+    uint32_t *sbits;     // bit-packed fields (bit 1 = s +1)
+    int16_t *x;          // worldlines
+    int *hist;           // occupancy histogram (zero between sweeps)
+    double *logw;        // filter log-weights of the last sweep
+    int *anchor;         // per chain
+    MeasAcc *meas;       // per chain
+    double *sk;          // per chain N: sum of |m^(k)|^2 / N
+    unsigned long long *dens;  // per chain N: sum of n_up + n_dn per site (kept for diagnostics)
+    unsigned long long *sweep; // device sweep counter
+    unsigned *status;    // error bits
+};
+
+enum : unsigned { kStatusDegenerate = 1u, kStatusNonPositive = 2u, kStatusTimeout = 4u };
+
+// One launch of the FFBS kernel covers the chains of one lattice size.
+struct FfbsLaunch {
+    const int *class_chains;   // chain ids of this class
+    const int *class_pair_off; // [nclass + 1] prefix sums of 2*npair
+    int nclass;
+    int total_pairs;
+    int M_max;                 // largest M in the class (scratch slot size)
+    void *scratch;             // slots of M_max * L * L complex values
+    long long slot_elems;      // complex elements per slot
+};
+
+// Launchers (defined in the per-precision translation units).
+cudaError_t launch_ffbs(int L, bool fp64, const DevState &st, const FfbsLaunch &fl, int grid,
+                        int warps_per_cta, cudaStream_t stream);
+int ffbs_groups_per_warp(int L);
+size_t ffbs_smem_bytes(int L, bool fp64, int warps_per_cta);
+cudaError_t ffbs_occupancy(int L, bool fp64, int warps_per_cta, int *blocks_per_sm);
+bool ffbs_supported(int L);
+
+cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stream);
+cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int slices_per_cta,
+                         bool measure, cudaStream_t stream);
+cudaError_t configure_slice();
+cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
+cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
+                           double *sk_out, long long total_N, cudaStream_t stream);
+
+}  // namespace hqmc

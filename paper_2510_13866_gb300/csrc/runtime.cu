@@ -1,0 +1,897 @@
+// runtime.cu -- host side of the C ABI declared in include/hqmc.h: parameter validation,
+// FP64 tables, device layout, workspace, CUDA-graph capture of one sweep, read-outs.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hqmc.h"
+#include "internal.h"
+
+namespace hqmc {
+cudaError_t launch_ffbs_f32(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s);
+cudaError_t launch_ffbs_f64(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s);
+cudaError_t ffbs_occupancy_f32(int L, int wpc, int *blocks);
+cudaError_t ffbs_occupancy_f64(int L, int wpc, int *blocks);
+size_t ffbs_smem_f32(int L, int wpc);
+size_t ffbs_smem_f64(int L, int wpc);
+cudaError_t launch_grad(const DevState &st, bool fp64, int L, const int *class_chains, const int *class_wl_off,
+                        int nclass, int total_pairs, const void *v, void *dv, double *logz_wl, double *dt_wl,
+                        void *ckpt, long long ckpt_elems, int K, int grid, cudaStream_t s);
+size_t grad_ckpt_bytes_per_group(bool fp64, int L, int M);
+int grad_groups_per_cta(int L);
+bool grad_supported(int L);
+
+static const int kSizes[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+
+bool ffbs_supported(int L) {
+    for (int s : kSizes)
+        if (s == L) return true;
+    return false;
+}
+int ffbs_groups_per_warp(int L) { return L <= 4 ? 8 : L <= 8 ? 4 : L <= 16 ? 2 : 1; }
+}  // namespace hqmc
+
+using namespace hqmc;
+
+namespace {
+
+struct HostChain {
+    int L = 0, N = 0, M = 0, Nsig = 0;
+    uint64_t seed = 0;
+    double t = 0, U = 0, beta = 0, dtau = 0, filling = 0;
+    bool set = false;
+};
+
+struct LClass {
+    int L = 0;
+    std::vector<int> chains;
+    std::vector<int> pair_off;  // prefix sums of 2*npair
+    int total_pairs = 0;
+    int M_max = 0;
+    int grid = 0;          // CTAs launched
+    long long groups = 0;  // worldline groups launched
+    size_t scratch_off = 0;
+    size_t scratch_bytes = 0;
+    size_t cls_off = 0;    // device offset of the class arrays
+};
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct hqmc_ctx {
+    int device = 0;
+    int precision = HQMC_FP32;
+    int nchains = 0;
+    std::vector<HostChain> ch;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev;
+    bool use_graph = true, persistent = true;
+    int wpc = 0;
+    int num_sms = 0;
+    std::string err;
+
+    // device layout (valid when `ready`)
+    bool ready = false;       // layout built and state initialised
+    bool started = false;     // a sweep has run
+    bool own_mem = false;
+    unsigned char *base = nullptr;
+    size_t bytes = 0;
+    unsigned char *attached = nullptr;
+    size_t attached_bytes = 0;
+    std::vector<ChainDev> cdev;
+    std::vector<LClass> classes;
+    DevState st{};
+    size_t off_cr = 0, off_sko = 0, total_N = 0;
+    long long total_wl = 0;
+    double *d_cr = nullptr, *d_sko = nullptr;
+    uint64_t sweeps_host = 0;
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    // gradient resources
+    std::vector<int> grad_cls_off;
+
+    // per-phase timing: events [4 * slot]: ffbs start, ffbs end, slice start, slice end
+    int prof_max = 0, prof_n = 0;
+    std::vector<cudaEvent_t> prof_ev;
+};
+
+namespace {
+
+int fail(hqmc_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(hqmc_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, HQMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HQMC_CUDA(ctx, call)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// 1D ring propagator g(d) = [exp(z A)]_{0d}, A = ring adjacency, by its Taylor series
+// applied to a unit vector: every term is non-negative, so each entry is accurate to
+// rounding even where it is tiny.
+void ring_propagator(int L, double z, std::vector<double> &g) {
+    std::vector<double> term(L, 0.0), nxt(L, 0.0);
+    g.assign(L, 0.0);
+    term[0] = 1.0;
+    g[0] = 1.0;
+    for (int n = 1; n < 2000; ++n) {
+        double mx = 0.0;
+        for (int d = 0; d < L; ++d) {
+            const double v = term[(d + L - 1) % L] + term[(d + 1) % L];
+            nxt[d] = v * z / n;
+            mx = std::max(mx, nxt[d]);
+        }
+        term.swap(nxt);
+        for (int d = 0; d < L; ++d) g[d] += term[d];
+        if (n > 2 * L + 8 && mx < 1e-300) break;
+        if (mx == 0.0) break;
+    }
+}
+
+void build_tab(const HostChain &h, ChainTab &tb, double lam) {
+    std::memset(&tb, 0, sizeof(tb));
+    const int L = h.L;
+    const double z = h.t * h.dtau;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < L; ++k) {
+        const double ck = std::cos(two_pi * k / L);
+        const double gh = std::exp(2.0 * z * ck);
+        tb.ghat_d[k] = gh / L;
+        tb.ghat_f[k] = float(gh / L);
+        tb.dghat_d[k] = 2.0 * h.dtau * ck * gh / L;
+        tb.dghat_f[k] = float(tb.dghat_d[k]);
+    }
+    std::vector<double> g;
+    ring_propagator(L, z, g);
+    for (int d = 0; d < L; ++d) {
+        tb.g_d[d] = g[d];
+        tb.g_f[d] = float(g[d]);
+        // d/dt exp(t dtau A) = dtau A exp(t dtau A)  =>  g'(d) = dtau (g(d-1) + g(d+1))
+        const double dg = h.dtau * (g[(d + L - 1) % L] + g[(d + 1) % L]);
+        const double hv = g[d] > 0.0 ? dg / g[d] : 0.0;
+        tb.h_d[d] = hv;
+        tb.h_f[d] = float(hv);
+    }
+    for (int m = -kPTab; m <= kPTab; ++m) tb.pplus[m + kPTab] = 1.0 / (1.0 + std::exp(-2.0 * lam * m));
+}
+
+double hirsch_lambda(double U, double dtau) { return std::acosh(std::exp(0.5 * dtau * U)); }
+
+int check_params(hqmc_ctx *c, int L, double t, double U, double beta, double dtau, double filling, int *M,
+                 int *Nsig) {
+    if (!(t >= 0.0) || !std::isfinite(t)) return fail(c, HQMC_ERR_ARG, "t must be finite and >= 0");
+    if (!(U >= 0.0) || !std::isfinite(U)) return fail(c, HQMC_ERR_ARG, "U must be finite and >= 0 (U < 0 needs the Gaussian field)");
+    if (!(beta > 0.0) || !(dtau > 0.0) || !std::isfinite(beta) || !std::isfinite(dtau))
+        return fail(c, HQMC_ERR_ARG, "beta and dtau must be positive");
+    const double mr = beta / dtau;
+    const long long m = llround(mr);
+    if (m < 1 || std::fabs(double(m) * dtau - beta) > 1e-9 * std::max(1.0, beta))
+        return fail(c, HQMC_ERR_ARG, "beta/dtau must be an integer");
+    if (m > 32767) return fail(c, HQMC_ERR_ARG, "too many slices");
+    const double ns = filling * L * L / 2.0;
+    const long long n = llround(ns);
+    if (!(filling > 0.0) || std::fabs(ns - double(n)) > 1e-9 || n < 1 || n > (long long)L * L)
+        return fail(c, HQMC_ERR_ARG, "filling*N/2 must be an integer in [1, N]");
+    *M = int(m);
+    *Nsig = int(n);
+    return HQMC_OK;
+}
+
+void drop_graph(hqmc_ctx *c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+}
+
+void free_layout(hqmc_ctx *c) {
+    drop_graph(c);
+    if (c->own_mem && c->base) cudaFree(c->base);
+    c->base = nullptr;
+    c->own_mem = false;
+    c->ready = false;
+}
+
+int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
+    cudaError_t e = c->precision == HQMC_FP64 ? ffbs_occupancy_f64(L, wpc, blocks) : ffbs_occupancy_f32(L, wpc, blocks);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    if (*blocks < 1) *blocks = 1;
+    return HQMC_OK;
+}
+
+int default_wpc(hqmc_ctx *c, int L) {
+    if (c->wpc > 0) return c->wpc;
+    return c->precision == HQMC_FP64 ? 4 : 4;
+}
+
+// Compute the device layout (offsets) and its size; fills c->classes, c->cdev.
+int plan_layout(hqmc_ctx *c, size_t *total) {
+    const int nc = c->nchains;
+    for (int i = 0; i < nc; ++i)
+        if (!c->ch[i].set) return fail(c, HQMC_ERR_STATE, "set_params has not been called for every chain");
+    const bool f64 = c->precision == HQMC_FP64;
+    c->cdev.assign(nc, ChainDev{});
+    // classes by L
+    c->classes.clear();
+    for (int i = 0; i < nc; ++i) {
+        auto it = std::find_if(c->classes.begin(), c->classes.end(), [&](const LClass &k) { return k.L == c->ch[i].L; });
+        if (it == c->classes.end()) {
+            c->classes.push_back(LClass{});
+            c->classes.back().L = c->ch[i].L;
+            it = c->classes.end() - 1;
+        }
+        it->chains.push_back(i);
+    }
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        off = round_up(off, 256);
+        const size_t o = off;
+        off += b;
+        return o;
+    };
+    const size_t o_chains = take(sizeof(ChainDev) * nc);
+    const size_t o_tabs = take(sizeof(ChainTab) * nc);
+    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0;
+    for (int i = 0; i < nc; ++i) {
+        const HostChain &h = c->ch[i];
+        ChainDev &d = c->cdev[i];
+        d.L = h.L;
+        d.N = h.N;
+        d.M = h.M;
+        d.Nsig = h.Nsig;
+        d.npair = (h.Nsig + 1) / 2;
+        d.wpl = (h.L + 31) / 32;
+        d.seed = h.seed;
+        d.lam = hirsch_lambda(h.U, h.dtau);
+        d.w_plus[0] = std::exp(d.lam);
+        d.w_minus[0] = std::exp(-d.lam);
+        d.w_plus[1] = std::exp(-d.lam);
+        d.w_minus[1] = std::exp(d.lam);
+        d.t = h.t;
+        d.beta = h.beta;
+        d.s_off = sb;
+        sb += 2LL * h.M * h.L * d.wpl;
+        d.x_off = xb;
+        xb += 2LL * h.Nsig * h.M;
+        d.h_off = hb;
+        hb += 2LL * h.M * h.N;
+        d.logw_off = lb;
+        lb += 2LL * h.Nsig;
+        d.v_off = vb;
+        vb += 2LL * h.M * h.N;
+        d.meas_off = mb;
+        mb += h.N;
+    }
+    c->total_N = size_t(mb);
+    c->total_wl = lb;
+    const size_t o_s = take(size_t(sb) * 4);
+    const size_t o_x = take(size_t(xb) * 2);
+    const size_t o_h = take(size_t(hb) * 4);
+    const size_t o_l = take(size_t(lb) * 8);
+    const size_t o_a = take(size_t(nc) * 4);
+    const size_t o_m = take(sizeof(MeasAcc) * nc);
+    const size_t o_sk = take(size_t(mb) * 8);
+    const size_t o_dn = take(size_t(mb) * 8);
+    const size_t o_sw = take(8);
+    const size_t o_stt = take(8);
+    c->off_cr = take(size_t(mb) * 8);
+    c->off_sko = take(size_t(mb) * 8);
+    // classes
+    for (auto &k : c->classes) {
+        k.pair_off.assign(1, 0);
+        k.M_max = 0;
+        for (int ci : k.chains) {
+            k.pair_off.push_back(k.pair_off.back() + 2 * c->cdev[ci].npair);
+            k.M_max = std::max(k.M_max, c->cdev[ci].M);
+        }
+        k.total_pairs = k.pair_off.back();
+        k.cls_off = take(sizeof(int) * (k.chains.size() + k.pair_off.size()));
+    }
+    // FFBS grid and scratch per class
+    double total_work = 0.0;
+    for (auto &k : c->classes) total_work += double(k.total_pairs) * k.M_max * k.L * k.L * std::log2(double(k.L) + 1);
+    for (auto &k : c->classes) {
+        const int wpc = default_wpc(c, k.L);
+        const int gpc = wpc * ffbs_groups_per_warp(k.L);
+        const int need = (k.total_pairs + gpc - 1) / gpc;
+        int grid = need;
+        if (c->persistent) {
+            int bps = 1;
+            int rc = occupancy(c, k.L, wpc, &bps);
+            if (rc) return rc;
+            const double share = total_work > 0 ? double(k.total_pairs) * k.M_max * k.L * k.L * std::log2(double(k.L) + 1) / total_work : 1.0;
+            const int cap = std::max(1, int(std::lround(double(bps) * c->num_sms * share)));
+            grid = std::min(need, cap);
+        }
+        k.grid = std::max(1, grid);
+        k.groups = (long long)k.grid * gpc;
+        const size_t elem = f64 ? 16 : 8;
+        k.scratch_bytes = size_t(k.groups) * k.M_max * k.L * k.L * elem;
+        k.scratch_off = take(k.scratch_bytes);
+    }
+    *total = round_up(off, 256);
+    // keep the offsets for binding
+    c->st = DevState{};
+    c->st.chains = reinterpret_cast<const ChainDev *>(o_chains);
+    c->st.tabs = reinterpret_cast<const ChainTab *>(o_tabs);
+    c->st.sbits = reinterpret_cast<uint32_t *>(o_s);
+    c->st.x = reinterpret_cast<int16_t *>(o_x);
+    c->st.hist = reinterpret_cast<int *>(o_h);
+    c->st.logw = reinterpret_cast<double *>(o_l);
+    c->st.anchor = reinterpret_cast<int *>(o_a);
+    c->st.meas = reinterpret_cast<MeasAcc *>(o_m);
+    c->st.sk = reinterpret_cast<double *>(o_sk);
+    c->st.dens = reinterpret_cast<unsigned long long *>(o_dn);
+    c->st.sweep = reinterpret_cast<unsigned long long *>(o_sw);
+    c->st.status = reinterpret_cast<unsigned *>(o_stt);
+    return HQMC_OK;
+}
+
+template <typename P>
+P rebase(P p, unsigned char *base) {
+    return reinterpret_cast<P>(base + reinterpret_cast<size_t>(p));
+}
+
+// Plan, bind memory (attached or owned), upload tables and initialise the state.
+int prepare(hqmc_ctx *c) {
+    if (c->ready) return HQMC_OK;
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    size_t need = 0;
+    int rc = plan_layout(c, &need);
+    if (rc) return rc;
+    if (c->attached) {
+        if (c->attached_bytes < need) return fail(c, HQMC_ERR_NOMEM, "attached workspace too small");
+        c->base = c->attached;
+        c->own_mem = false;
+    } else {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, HQMC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        c->base = static_cast<unsigned char *>(p);
+        c->own_mem = true;
+    }
+    c->bytes = need;
+    DevState &s = c->st;
+    s.chains = rebase(s.chains, c->base);
+    s.tabs = rebase(s.tabs, c->base);
+    s.sbits = rebase(s.sbits, c->base);
+    s.x = rebase(s.x, c->base);
+    s.hist = rebase(s.hist, c->base);
+    s.logw = rebase(s.logw, c->base);
+    s.anchor = rebase(s.anchor, c->base);
+    s.meas = rebase(s.meas, c->base);
+    s.sk = rebase(s.sk, c->base);
+    s.dens = rebase(s.dens, c->base);
+    s.sweep = rebase(s.sweep, c->base);
+    s.status = rebase(s.status, c->base);
+    c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
+    c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
+    cudaStream_t st = c->stream;
+    HQMC_CUDA(c, cudaMemsetAsync(c->base, 0, need, st));
+    std::vector<ChainTab> tabs(c->nchains);
+    for (int i = 0; i < c->nchains; ++i) build_tab(c->ch[i], tabs[i], c->cdev[i].lam);
+    HQMC_CUDA(c, cudaMemcpyAsync((void *)s.chains, c->cdev.data(), sizeof(ChainDev) * c->nchains, cudaMemcpyHostToDevice, st));
+    HQMC_CUDA(c, cudaMemcpyAsync((void *)s.tabs, tabs.data(), sizeof(ChainTab) * c->nchains, cudaMemcpyHostToDevice, st));
+    for (auto &k : c->classes) {
+        std::vector<int> buf(k.chains);
+        buf.insert(buf.end(), k.pair_off.begin(), k.pair_off.end());
+        HQMC_CUDA(c, cudaMemcpyAsync(c->base + k.cls_off, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice, st));
+    }
+    // kernel attributes are set here, outside any stream capture
+    for (auto &k : c->classes) {
+        int bps = 0;
+        rc = occupancy(c, k.L, default_wpc(c, k.L), &bps);
+        if (rc) return rc;
+    }
+    HQMC_CUDA(c, configure_slice());
+    cudaError_t e = launch_init_state(s, c->nchains, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init_state");
+    HQMC_CUDA(c, cudaStreamSynchronize(st));
+    c->sweeps_host = 0;
+    c->ready = true;
+    c->started = false;
+    return HQMC_OK;
+}
+
+int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
+    const bool f64 = c->precision == HQMC_FP64;
+    const int nk = int(c->classes.size());
+    const bool prof = !capture && c->prof_max > 0 && c->prof_n < c->prof_max;
+    cudaEvent_t *pe = prof ? &c->prof_ev[4 * size_t(c->prof_n)] : nullptr;
+    if (prof) HQMC_CUDA(c, cudaEventRecord(pe[0], st));
+    // fork: class k > 0 on aux stream k-1
+    if (nk > 1) {
+        while ((int)c->aux.size() < nk - 1) {
+            cudaStream_t s;
+            HQMC_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            c->aux.push_back(s);
+        }
+        while ((int)c->ev.size() < 2 * nk) {
+            cudaEvent_t e;
+            HQMC_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->ev.push_back(e);
+        }
+        HQMC_CUDA(c, cudaEventRecord(c->ev[0], st));
+        for (int k = 1; k < nk; ++k) HQMC_CUDA(c, cudaStreamWaitEvent(c->aux[k - 1], c->ev[0], 0));
+    }
+    (void)capture;
+    for (int k = 0; k < nk; ++k) {
+        LClass &cl = c->classes[k];
+        FfbsLaunch fl{};
+        fl.class_chains = reinterpret_cast<const int *>(c->base + cl.cls_off);
+        fl.class_pair_off = fl.class_chains + cl.chains.size();
+        fl.nclass = int(cl.chains.size());
+        fl.total_pairs = cl.total_pairs;
+        fl.M_max = cl.M_max;
+        fl.scratch = c->base + cl.scratch_off;
+        fl.slot_elems = (long long)cl.M_max * cl.L * cl.L;
+        cudaStream_t s = k == 0 ? st : c->aux[k - 1];
+        const int wpc = default_wpc(c, cl.L);
+        cudaError_t e = f64 ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
+                            : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ffbs launch");
+    }
+    if (nk > 1) {
+        for (int k = 1; k < nk; ++k) {
+            HQMC_CUDA(c, cudaEventRecord(c->ev[k], c->aux[k - 1]));
+            HQMC_CUDA(c, cudaStreamWaitEvent(st, c->ev[k], 0));
+        }
+    }
+    if (prof) HQMC_CUDA(c, cudaEventRecord(pe[1], st));
+    int max_M = 0;
+    for (auto &d : c->cdev) max_M = std::max(max_M, d.M);
+    if (prof) HQMC_CUDA(c, cudaEventRecord(pe[2], st));
+    cudaError_t e = launch_slice(c->st, c->nchains, max_M, 8, true, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
+    if (prof) {
+        HQMC_CUDA(c, cudaEventRecord(pe[3], st));
+        ++c->prof_n;
+    }
+    e = launch_advance(c->st, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
+    return HQMC_OK;
+}
+
+int check_status(hqmc_ctx *c) {
+    unsigned stt = 0;
+    HQMC_CUDA(c, cudaMemcpyAsync(&stt, c->st.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (stt) {
+        HQMC_CUDA(c, cudaMemsetAsync(c->st.status, 0, sizeof(unsigned), c->stream));
+        if (stt & kStatusTimeout) return fail(c, HQMC_ERR_TIMEOUT, "device wait expired");
+        return fail(c, HQMC_ERR_NUMERIC,
+                    (stt & kStatusDegenerate) ? "a draw met an all-zero CDF" : "log Z met a non-positive amplitude");
+    }
+    return HQMC_OK;
+}
+
+}  // namespace
+
+#pragma GCC visibility push(default)
+extern "C" {
+
+const char *hqmc_strerror(int code) {
+    switch (code) {
+        case HQMC_OK: return "ok";
+        case HQMC_ERR_ARG: return "invalid argument";
+        case HQMC_ERR_NOMEM: return "out of device memory";
+        case HQMC_ERR_CUDA: return "CUDA runtime error";
+        case HQMC_ERR_TIMEOUT: return "device wait timed out";
+        case HQMC_ERR_STATE: return "call out of order";
+        case HQMC_ERR_UNSUPPORTED: return "unsupported lattice size or mode";
+        case HQMC_ERR_NUMERIC: return "numerical degeneracy";
+        default: return "unknown error";
+    }
+}
+
+const char *hqmc_last_error_detail(hqmc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int hqmc_supported_L(int *out, int cap) {
+    int n = 0;
+    for (int s : kSizes) {
+        if (out && n < cap) out[n] = s;
+        ++n;
+    }
+    return n;
+}
+
+int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t *seeds, int precision, int device) {
+    if (!out || !L || !seeds || n_chains < 1) return HQMC_ERR_ARG;
+    if (precision != HQMC_FP32 && precision != HQMC_FP64) return HQMC_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n_chains; ++i) {
+        if (L[i] < 2) return HQMC_ERR_ARG;
+        if (!ffbs_supported(L[i])) return HQMC_ERR_UNSUPPORTED;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return HQMC_ERR_CUDA;
+    }
+    hqmc_ctx *c = new hqmc_ctx();
+    c->device = device;
+    c->precision = precision;
+    c->nchains = n_chains;
+    c->ch.resize(n_chains);
+    for (int i = 0; i < n_chains; ++i) {
+        c->ch[i].L = L[i];
+        c->ch[i].N = L[i] * L[i];
+        c->ch[i].seed = seeds[i];
+    }
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return HQMC_ERR_CUDA;
+    }
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return HQMC_ERR_CUDA;
+    }
+    c->own_stream = true;
+    if (precision == HQMC_FP64) {
+        c->use_graph = false;
+        c->persistent = false;
+    }
+    *out = c;
+    return HQMC_OK;
+}
+
+int hqmc_set_params(hqmc_ctx *c, int chain, double t, double U, double beta, double dtau, double filling) {
+    if (!c) return HQMC_ERR_ARG;
+    if (chain < -1 || chain >= c->nchains) return fail(c, HQMC_ERR_ARG, "chain index out of range");
+    const int lo = chain < 0 ? 0 : chain, hi = chain < 0 ? c->nchains : chain + 1;
+    for (int i = lo; i < hi; ++i) {
+        int M = 0, Ns = 0;
+        int rc = check_params(c, c->ch[i].L, t, U, beta, dtau, filling, &M, &Ns);
+        if (rc) return rc;
+        if (c->ready && (M != c->ch[i].M || Ns != c->ch[i].Nsig))
+            return fail(c, HQMC_ERR_STATE, "M and Nsig are fixed once the state exists");
+    }
+    for (int i = lo; i < hi; ++i) {
+        HostChain &h = c->ch[i];
+        int M = 0, Ns = 0;
+        check_params(c, h.L, t, U, beta, dtau, filling, &M, &Ns);
+        h.t = t;
+        h.U = U;
+        h.beta = beta;
+        h.dtau = dtau;
+        h.filling = filling;
+        h.M = M;
+        h.Nsig = Ns;
+        h.set = true;
+    }
+    if (c->ready) {
+        // refresh per-chain tables and constants in place (shape unchanged)
+        for (int i = lo; i < hi; ++i) {
+            ChainDev &d = c->cdev[i];
+            d.lam = hirsch_lambda(c->ch[i].U, c->ch[i].dtau);
+            d.w_plus[0] = std::exp(d.lam);
+            d.w_minus[0] = std::exp(-d.lam);
+            d.w_plus[1] = std::exp(-d.lam);
+            d.w_minus[1] = std::exp(d.lam);
+            d.t = c->ch[i].t;
+            d.beta = c->ch[i].beta;
+            ChainTab tb;
+            build_tab(c->ch[i], tb, d.lam);
+            HQMC_CUDA(c, cudaMemcpyAsync((void *)(c->st.chains + i), &d, sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
+            HQMC_CUDA(c, cudaMemcpyAsync((void *)(c->st.tabs + i), &tb, sizeof(ChainTab), cudaMemcpyHostToDevice, c->stream));
+        }
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return HQMC_OK;
+}
+
+int hqmc_set_stream(hqmc_ctx *c, void *stream) {
+    if (!c) return HQMC_ERR_ARG;
+    drop_graph(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->own_stream = false;
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (!c->stream) {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return HQMC_ERR_CUDA;
+        c->own_stream = true;
+    }
+    return HQMC_OK;
+}
+
+int hqmc_set_launch(hqmc_ctx *c, int use_graph, int persistent, int warps_per_cta) {
+    if (!c) return HQMC_ERR_ARG;
+    if (warps_per_cta != 0 && warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8 &&
+        warps_per_cta != 16)
+        return fail(c, HQMC_ERR_ARG, "warps_per_cta must be 0, 1, 2, 4, 8 or 16");
+    const bool relayout = (bool(persistent) != c->persistent) || (warps_per_cta != c->wpc);
+    c->use_graph = use_graph != 0;
+    c->persistent = persistent != 0;
+    c->wpc = warps_per_cta;
+    drop_graph(c);
+    if (relayout && c->ready) {
+        // the scratch size depends on the grid: rebuild the layout but keep the state
+        std::vector<int8_t> s_save;
+        std::vector<uint32_t> bits;
+        std::vector<int16_t> xs;
+        size_t sb = 0, xb = 0;
+        for (auto &d : c->cdev) {
+            sb += 2ull * d.M * d.L * d.wpl;
+            xb += 2ull * d.Nsig * d.M;
+        }
+        bits.resize(sb);
+        xs.resize(xb);
+        unsigned long long sw = 0;
+        HQMC_CUDA(c, cudaMemcpy(bits.data(), c->st.sbits, sb * 4, cudaMemcpyDeviceToHost));
+        HQMC_CUDA(c, cudaMemcpy(xs.data(), c->st.x, xb * 2, cudaMemcpyDeviceToHost));
+        HQMC_CUDA(c, cudaMemcpy(&sw, c->st.sweep, 8, cudaMemcpyDeviceToHost));
+        const bool started = c->started;
+        free_layout(c);
+        int rc = prepare(c);
+        if (rc) return rc;
+        HQMC_CUDA(c, cudaMemcpy(c->st.sbits, bits.data(), sb * 4, cudaMemcpyHostToDevice));
+        HQMC_CUDA(c, cudaMemcpy(c->st.x, xs.data(), xb * 2, cudaMemcpyHostToDevice));
+        HQMC_CUDA(c, cudaMemcpy(c->st.sweep, &sw, 8, cudaMemcpyHostToDevice));
+        c->sweeps_host = sw;
+        c->started = started;
+    }
+    return HQMC_OK;
+}
+
+int hqmc_workspace_size(hqmc_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return HQMC_ERR_ARG;
+    size_t need = 0;
+    DevState keep = c->st;
+    auto keep_cdev = c->cdev;
+    auto keep_cls = c->classes;
+    int rc = plan_layout(c, &need);
+    if (c->ready) {
+        c->st = keep;
+        c->cdev = keep_cdev;
+        c->classes = keep_cls;
+    }
+    if (rc) return rc;
+    *bytes = need;
+    return HQMC_OK;
+}
+
+int hqmc_attach_workspace(hqmc_ctx *c, void *dev_ptr, size_t bytes) {
+    if (!c || !dev_ptr) return HQMC_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(c, HQMC_ERR_ARG, "workspace must be 256-byte aligned");
+    free_layout(c);
+    c->attached = static_cast<unsigned char *>(dev_ptr);
+    c->attached_bytes = bytes;
+    size_t need = 0;
+    int rc = plan_layout(c, &need);
+    if (rc) return rc;
+    if (bytes < need) {
+        c->attached = nullptr;
+        c->attached_bytes = 0;
+        return fail(c, HQMC_ERR_NOMEM, "workspace smaller than hqmc_workspace_size");
+    }
+    return prepare(c);
+}
+
+int hqmc_sweep(hqmc_ctx *c, int n_sweeps, double *logw_out) {
+    if (!c || n_sweeps < 0) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    if (c->use_graph && c->prof_max == 0 && !c->exec && n_sweeps > 0) {
+        HQMC_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_sweep(c, c->stream, true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        c->graph = g;
+        e = cudaGraphInstantiate(&c->exec, g, 0);
+        if (e != cudaSuccess) {
+            drop_graph(c);
+            return cuda_fail(c, e, "graph instantiate");
+        }
+    }
+    const bool graph = c->use_graph && c->prof_max == 0;
+    for (int i = 0; i < n_sweeps; ++i) {
+        if (graph) {
+            HQMC_CUDA(c, cudaGraphLaunch(c->exec, c->stream));
+        } else {
+            rc = enqueue_sweep(c, c->stream, false);
+            if (rc) return rc;
+        }
+    }
+    c->sweeps_host += n_sweeps;
+    if (n_sweeps > 0) c->started = true;
+    if (logw_out)
+        HQMC_CUDA(c, cudaMemcpyAsync(logw_out, c->st.logw, sizeof(double) * c->total_wl, cudaMemcpyDeviceToHost, c->stream));
+    return check_status(c);
+}
+
+int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) {
+    if (!c) return HQMC_ERR_ARG;
+    if (!c->ready) return fail(c, HQMC_ERR_STATE, "no state yet");
+    int max_N = 0;
+    for (auto &d : c->cdev) max_N = std::max(max_N, d.N);
+    cudaError_t e = launch_readout(c->st, c->nchains, max_N, c->d_cr, c->d_sko, (long long)c->total_N, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "readout");
+    std::vector<MeasAcc> acc(c->nchains);
+    HQMC_CUDA(c, cudaMemcpyAsync(acc.data(), c->st.meas, sizeof(MeasAcc) * c->nchains, cudaMemcpyDeviceToHost, c->stream));
+    if (Sk) HQMC_CUDA(c, cudaMemcpyAsync(Sk, c->d_sko, 8 * c->total_N, cudaMemcpyDeviceToHost, c->stream));
+    if (Cr) HQMC_CUDA(c, cudaMemcpyAsync(Cr, c->d_cr, 8 * c->total_N, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> skh(c->total_N);
+    HQMC_CUDA(c, cudaMemcpyAsync(skh.data(), c->d_sko, 8 * c->total_N, cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (out) {
+        for (int i = 0; i < c->nchains; ++i) {
+            const ChainDev &d = c->cdev[i];
+            const double ns = double(acc[i].samples);
+            const double denom = ns * d.M * d.N;
+            hqmc_obs &o = out[i];
+            o.n_samples = (int64_t)acc[i].samples;
+            o.density = denom > 0 ? double(acc[i].n_sum) / denom : 0.0;
+            o.double_occ = denom > 0 ? double(acc[i].d_sum) / denom : 0.0;
+            o.m2 = denom > 0 ? double(acc[i].m2_sum) / denom : 0.0;
+            o.ekin = ns > 0 ? -(c->ch[i].t / c->ch[i].beta) * acc[i].link_sum / (ns * d.N) : 0.0;
+            const int kh = d.L / 2;
+            o.s_pipi = skh[d.meas_off + kh + d.L * kh];
+        }
+    }
+    if (reset) {
+        HQMC_CUDA(c, cudaMemsetAsync(c->st.meas, 0, sizeof(MeasAcc) * c->nchains, c->stream));
+        HQMC_CUDA(c, cudaMemsetAsync(c->st.sk, 0, 8 * c->total_N, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return HQMC_OK;
+}
+
+int hqmc_chain_shape(hqmc_ctx *c, int chain, int *L, int *M, int *Nsig) {
+    if (!c || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
+    if (L) *L = c->ch[chain].L;
+    if (M) *M = c->ch[chain].M;
+    if (Nsig) *Nsig = c->ch[chain].Nsig;
+    return HQMC_OK;
+}
+
+int hqmc_get_state(hqmc_ctx *c, int chain, int8_t *s, int32_t *x, int *anchor, uint64_t *sweeps) {
+    if (!c || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    if (s) {
+        std::vector<uint32_t> bits(size_t(d.M) * d.L * d.wpl);
+        HQMC_CUDA(c, cudaMemcpyAsync(bits.data(), c->st.sbits + d.s_off, bits.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int l = 0; l < d.M; ++l)
+            for (int iy = 0; iy < d.L; ++iy)
+                for (int ix = 0; ix < d.L; ++ix) {
+                    const uint32_t w = bits[(size_t(l) * d.L + iy) * d.wpl + (ix >> 5)];
+                    s[size_t(l) * d.N + ix + d.L * iy] = ((w >> (ix & 31)) & 1u) ? 1 : -1;
+                }
+    }
+    if (x) {
+        std::vector<int16_t> xs(2ull * d.Nsig * d.M);
+        HQMC_CUDA(c, cudaMemcpyAsync(xs.data(), c->st.x + d.x_off, xs.size() * 2, cudaMemcpyDeviceToHost, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t k = 0; k < xs.size(); ++k) x[k] = xs[k];
+    }
+    if (anchor) {
+        HQMC_CUDA(c, cudaMemcpyAsync(anchor, c->st.anchor + chain, 4, cudaMemcpyDeviceToHost, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (sweeps) {
+        unsigned long long sw = 0;
+        HQMC_CUDA(c, cudaMemcpyAsync(&sw, c->st.sweep, 8, cudaMemcpyDeviceToHost, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+        *sweeps = sw;
+    }
+    return HQMC_OK;
+}
+
+int hqmc_set_state(hqmc_ctx *c, int chain, const int8_t *s, const int32_t *x, const uint64_t *sweeps) {
+    if (!c || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    if (s) {
+        std::vector<uint32_t> rows(size_t(d.M) * d.L * d.wpl, 0u), cols(rows.size(), 0u);
+        for (int l = 0; l < d.M; ++l)
+            for (int iy = 0; iy < d.L; ++iy)
+                for (int ix = 0; ix < d.L; ++ix) {
+                    const int8_t v = s[size_t(l) * d.N + ix + d.L * iy];
+                    if (v != 1 && v != -1) return fail(c, HQMC_ERR_ARG, "field values must be +1 or -1");
+                    if (v == 1) {
+                        rows[(size_t(l) * d.L + iy) * d.wpl + (ix >> 5)] |= 1u << (ix & 31);
+                        cols[(size_t(l) * d.L + ix) * d.wpl + (iy >> 5)] |= 1u << (iy & 31);
+                    }
+                }
+        HQMC_CUDA(c, cudaMemcpyAsync(c->st.sbits + d.s_off, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        HQMC_CUDA(c, cudaMemcpyAsync(c->st.sbits + d.s_off + rows.size(), cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (x) {
+        std::vector<int16_t> xs(2ull * d.Nsig * d.M);
+        for (size_t k = 0; k < xs.size(); ++k) {
+            if (x[k] < 0 || x[k] >= d.N) return fail(c, HQMC_ERR_ARG, "site index out of range");
+            xs[k] = int16_t(x[k]);
+        }
+        HQMC_CUDA(c, cudaMemcpyAsync(c->st.x + d.x_off, xs.data(), xs.size() * 2, cudaMemcpyHostToDevice, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (sweeps) {
+        unsigned long long sw = *sweeps;
+        HQMC_CUDA(c, cudaMemcpyAsync(c->st.sweep, &sw, 8, cudaMemcpyHostToDevice, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->sweeps_host = sw;
+    }
+    return HQMC_OK;
+}
+
+int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_dv, double *dlogZ_dt) {
+    (void)v;
+    (void)logZ;
+    (void)dlogZ_dv;
+    (void)dlogZ_dt;
+    if (!c) return HQMC_ERR_ARG;
+    return fail(c, HQMC_ERR_UNSUPPORTED, "log_weight_grad is not built yet");
+}
+
+int hqmc_set_profiling(hqmc_ctx *c, int max_sweeps) {
+    if (!c || max_sweeps < 0) return HQMC_ERR_ARG;
+    for (auto e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_max = 0;
+    c->prof_n = 0;
+    if (max_sweeps > 0) {
+        c->prof_ev.resize(4 * size_t(max_sweeps));
+        for (auto &e : c->prof_ev) HQMC_CUDA(c, cudaEventCreate(&e));
+        c->prof_max = max_sweeps;
+    }
+    return HQMC_OK;
+}
+
+int hqmc_profile_read(hqmc_ctx *c, double *ffbs_ms, double *slice_ms, int *n_sweeps) {
+    if (!c) return HQMC_ERR_ARG;
+    if (c->prof_max == 0) return fail(c, HQMC_ERR_STATE, "profiling is off");
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    double fs = 0.0, ss = 0.0;
+    for (int i = 0; i < c->prof_n; ++i) {
+        float a = 0.f, b = 0.f;
+        HQMC_CUDA(c, cudaEventElapsedTime(&a, c->prof_ev[4 * i], c->prof_ev[4 * i + 1]));
+        HQMC_CUDA(c, cudaEventElapsedTime(&b, c->prof_ev[4 * i + 2], c->prof_ev[4 * i + 3]));
+        fs += a;
+        ss += b;
+    }
+    if (ffbs_ms) *ffbs_ms = fs;
+    if (slice_ms) *slice_ms = ss;
+    if (n_sweeps) *n_sweeps = c->prof_n;
+    c->prof_n = 0;
+    return HQMC_OK;
+}
+
+void hqmc_destroy(hqmc_ctx *c) {
+    if (!c) return;
+    for (auto e : c->prof_ev) cudaEventDestroy(e);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_layout(c);
+    for (auto s : c->aux) cudaStreamDestroy(s);
+    for (auto e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

@@ -1,0 +1,293 @@
+// slice.cu -- site-parallel kernels: the Hirsch-field Gibbs resample fused with the
+// observable accumulation (Sec. 3.5.4 and Sec. 4), state initialisation, the sweep
+// counter and the observable read-out.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace hqmc {
+
+namespace {
+
+constexpr int kSliceThreads = 256;
+constexpr int kSkSmemMaxN = 4096;  // S(k) accumulated in shared memory up to L = 64
+
+// Block-wide sum of an unsigned 64-bit value into *dst (one atomic per block).
+__device__ void block_add_u64(unsigned long long v, unsigned long long *dst, unsigned long long *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    __syncthreads();
+    if (ln == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+        if (s) atomicAdd(dst, s);
+    }
+}
+
+struct SliceSmem {
+    size_t rows, red, ms, x1, tw, sk, total;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+// byte offsets of the slice kernel's shared arrays for lattice size L
+__host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl) {
+    const size_t N = size_t(L) * L;
+    SliceSmem s{};
+    s.rows = 0;
+    s.red = align16(s.rows + 2 * size_t(L) * wpl * 4);
+    s.ms = align16(s.red + 32 * 8);
+    if (N <= size_t(kSkSmemMaxN)) {
+        s.x1 = align16(s.ms + N * 4);
+        s.tw = align16(s.x1 + N * 8);
+        s.sk = align16(s.tw + size_t(L) * 8);
+        s.total = align16(s.sk + N * 8);
+    } else {
+        s.x1 = s.tw = s.sk = s.ms;
+        s.total = s.ms;
+    }
+    return s;
+}
+
+}  // namespace
+
+// One CTA per (chain, group of slices).  For every site of a slice:
+//   m = n_up - n_dn;  s = +1 iff u < P(s=+1|m) = 1/(1+exp(-2 lambda m))  (FP64 compare),
+// written bit-packed by rows and by columns; the histogram is cleared for the next
+// sweep.  With `measure`, the slice's n, n_up n_dn, m^2 and |m^(k)|^2/N are added to
+// the chain's accumulators (m^ by a direct separable DFT in FP32).
+__global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int slices_per_cta, int measure) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N, M = cd.M, wpl = cd.wpl;
+    const int l_begin = blockIdx.x * slices_per_cta;
+    if (l_begin >= M) return;
+    const int l_end = min(M, l_begin + slices_per_cta);
+    const uint64_t sweep = *st.sweep;
+    const double lam = cd.lam;
+    const ChainTab &tb = st.tabs[c];
+
+    const bool do_sk = measure && N <= kSkSmemMaxN;
+    const SliceSmem lay = slice_smem_layout(L, wpl);
+    uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
+    uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
+    float *ms = reinterpret_cast<float *>(smem_raw + lay.ms);            // [N] m of the slice
+    float2 *x1 = reinterpret_cast<float2 *>(smem_raw + lay.x1);          // [N] row DFT
+    float2 *tw = reinterpret_cast<float2 *>(smem_raw + lay.tw);          // [L] e^{-2 pi i j / L}
+    double *skacc = reinterpret_cast<double *>(smem_raw + lay.sk);       // [N]
+
+    for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+    if (do_sk) {
+        for (int j = threadIdx.x; j < L; j += blockDim.x) {
+            float s, co;
+            sincospif(2.0f * float(j) / float(L), &s, &co);
+            tw[j] = make_float2(co, -s);
+        }
+        for (int k = threadIdx.x; k < N; k += blockDim.x) skacc[k] = 0.0;
+    }
+    __syncthreads();
+
+    unsigned long long n_acc = 0, d_acc = 0, m2_acc = 0;
+    int *hu_base = st.hist + cd.h_off;
+    int *hd_base = hu_base + (long long)M * N;
+    uint32_t *srow_g = st.sbits + cd.s_off;
+    uint32_t *scol_g = srow_g + (long long)M * L * wpl;
+
+    for (int l = l_begin; l < l_end; ++l) {
+        int *hu = hu_base + (long long)l * N;
+        int *hd = hd_base + (long long)l * N;
+        const int nquads = (N + 3) >> 2;
+        for (int qd = threadIdx.x; qd < nquads; qd += blockDim.x) {
+            const u64x4 w4 = philox4x64_10((uint64_t)qd, (uint64_t)l, 1, sweep, cd.seed, 0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = 4 * qd + j;
+                if (x >= N) break;
+                const int nu = hu[x], nd = hd[x];
+                hu[x] = 0;
+                hd[x] = 0;
+                const int m = nu - nd;
+                const double pplus = (m >= -kPTab && m <= kPTab) ? tb.pplus[m + kPTab]
+                                                                  : 1.0 / (1.0 + exp(-2.0 * lam * m));
+                const bool up = u53(w4.v[j]) < pplus;
+                const int ix = x % L, iy = x / L;
+                if (up) {
+                    atomicOr(&rows[iy * wpl + (ix >> 5)], 1u << (ix & 31));
+                    atomicOr(&cols[ix * wpl + (iy >> 5)], 1u << (iy & 31));
+                }
+                if (measure) {
+                    n_acc += (unsigned long long)(nu + nd);
+                    d_acc += (unsigned long long)(nu * nd);
+                    m2_acc += (unsigned long long)(m * m);
+                    if (do_sk) ms[x] = float(m);
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < L * wpl; k += blockDim.x) {
+            srow_g[(long long)l * L * wpl + k] = rows[k];
+            scol_g[(long long)l * L * wpl + k] = cols[k];
+        }
+        if (do_sk) {
+            // x1[iy][kx] = sum_ix m[iy][ix] e^{-2 pi i kx ix / L}
+            for (int o = threadIdx.x; o < N; o += blockDim.x) {
+                const int kx = o % L, iy = o / L;
+                float re = 0.f, im = 0.f;
+                int ph = 0;
+                for (int ix = 0; ix < L; ++ix) {
+                    const float mv = ms[iy * L + ix];
+                    re += mv * tw[ph].x;
+                    im += mv * tw[ph].y;
+                    ph += kx;
+                    if (ph >= L) ph -= L;
+                }
+                x1[o] = make_float2(re, im);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+        if (do_sk) {
+            // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N
+            for (int o = threadIdx.x; o < N; o += blockDim.x) {
+                const int kx = o % L, ky = o / L;
+                float re = 0.f, im = 0.f;
+                int ph = 0;
+                for (int iy = 0; iy < L; ++iy) {
+                    const float2 a = x1[iy * L + kx], w = tw[ph];
+                    re += a.x * w.x - a.y * w.y;
+                    im += a.x * w.y + a.y * w.x;
+                    ph += ky;
+                    if (ph >= L) ph -= L;
+                }
+                skacc[o] += double(re * re + im * im) / double(N);
+            }
+        }
+        __syncthreads();
+    }
+    if (measure) {
+        MeasAcc &acc = st.meas[c];
+        block_add_u64(n_acc, &acc.n_sum, red);
+        block_add_u64(d_acc, &acc.d_sum, red);
+        block_add_u64(m2_acc, &acc.m2_sum, red);
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&acc.samples, 1ull);
+        if (do_sk)
+            for (int k = threadIdx.x; k < N; k += blockDim.x) atomicAdd(&st.sk[cd.meas_off + k], skacc[k]);
+    }
+}
+
+static size_t slice_smem_max() {
+    // the layout depends on L; size it for the largest layout any supported lattice needs
+    size_t sm = 0;
+    for (int L = 2; L <= kMaxL; ++L) {
+        const size_t t = slice_smem_layout(L, (L + 31) / 32).total;
+        sm = t > sm ? t : sm;
+    }
+    return sm;
+}
+
+cudaError_t configure_slice() {
+    return cudaFuncSetAttribute(slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slice_smem_max()));
+}
+
+cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int slices_per_cta, bool measure,
+                         cudaStream_t stream) {
+    const size_t sm = slice_smem_max();
+    dim3 grid((max_M + slices_per_cta - 1) / slices_per_cta, nchains);
+    slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, slices_per_cta, measure ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Initial state: s from Philox phase 3 (sweep = 2^64 - 1), +1 iff u < 1/2;
+// worldline p of the up spin on the p-th site of sublattice A ((ix+iy) even, row-major)
+// then of sublattice B, the down spin on B then A; every slice the same site.
+__global__ void init_fields_kernel(DevState st) {
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N, M = cd.M, wpl = cd.wpl;
+    uint32_t *srow = st.sbits + cd.s_off, *scol = srow + (long long)M * L * wpl;
+    for (int l = blockIdx.x; l < M; l += gridDim.x) {
+        for (int k = threadIdx.x; k < L * wpl; k += blockDim.x) {
+            srow[(long long)l * L * wpl + k] = 0u;
+            scol[(long long)l * L * wpl + k] = 0u;
+        }
+    }
+    __syncthreads();
+    for (int l = blockIdx.x; l < M; l += gridDim.x) {
+        for (int x = threadIdx.x; x < N; x += blockDim.x) {
+            const u64x4 w4 = philox4x64_10((uint64_t)(x >> 2), (uint64_t)l, 3, ~0ull, cd.seed, 0);
+            if (u53(w4.v[x & 3]) < 0.5) {
+                const int ix = x % L, iy = x / L;
+                atomicOr(&srow[((long long)l * L + iy) * wpl + (ix >> 5)], 1u << (ix & 31));
+                atomicOr(&scol[((long long)l * L + ix) * wpl + (iy >> 5)], 1u << (iy & 31));
+            }
+        }
+    }
+}
+
+__global__ void init_paths_kernel(DevState st) {
+    const int c = blockIdx.x;
+    const ChainDev &cd = st.chains[c];
+    const int sg = threadIdx.x;  // 0 up, 1 down
+    if (sg > 1) return;
+    const int L = cd.L, N = cd.N, M = cd.M;
+    int p = 0;
+    for (int pass = 0; pass < 2 && p < cd.Nsig; ++pass) {
+        const int want = (sg == 0) ? pass : 1 - pass;
+        for (int x = 0; x < N && p < cd.Nsig; ++x) {
+            if (((x % L) + (x / L)) % 2 != want) continue;
+            int16_t *xp = st.x + cd.x_off + ((long long)sg * cd.Nsig + p) * M;
+            for (int l = 0; l < M; ++l) xp[l] = int16_t(x);
+            ++p;
+        }
+    }
+    if (sg == 0) st.anchor[c] = -1;
+}
+
+cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stream) {
+    init_fields_kernel<<<dim3(1, nchains), 256, 0, stream>>>(st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    init_paths_kernel<<<nchains, 32, 0, stream>>>(st);
+    return cudaGetLastError();
+}
+
+__global__ void advance_kernel(DevState st) { *st.sweep += 1ull; }
+
+cudaError_t launch_advance(const DevState &st, cudaStream_t stream) {
+    advance_kernel<<<1, 1, 0, stream>>>(st);
+    return cudaGetLastError();
+}
+
+// C(r) = (1/N) sum_k cos(k.r) S(k) with S(k) = sk[k] / (4 samples M) (S^z = m/2).
+__global__ void readout_kernel(DevState st, double *cr_out, double *sk_out) {
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N;
+    const unsigned long long ns = st.meas[c].samples;
+    const double norm = ns ? 1.0 / (4.0 * double(ns) * cd.M) : 0.0;
+    const double *sk = st.sk + cd.meas_off;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
+        const int rx = r % L, ry = r / L;
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) {
+            const int kx = k % L, ky = k / L;
+            const int ph = (kx * rx + ky * ry) % L;
+            acc += sk[k] * cospi(2.0 * double(ph) / double(L));
+        }
+        cr_out[cd.meas_off + r] = acc * norm / N;
+        sk_out[cd.meas_off + r] = sk[r] * norm;
+    }
+}
+
+cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out, double *sk_out,
+                           long long /*total_N*/, cudaStream_t stream) {
+    dim3 grid((max_N + 255) / 256, nchains);
+    readout_kernel<<<grid, 256, 0, stream>>>(st, cr_out, sk_out);
+    return cudaGetLastError();
+}
+
+}  // namespace hqmc

