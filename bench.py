@@ -150,6 +150,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chains", type=int, default=WORK["chains"],
+                    help="chains per GPU (default 64; smaller values only for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -180,7 +182,8 @@ def main():
 
     from paper_2510_13866_gb300 import Lattice
 
-    w = WORK
+    w = dict(WORK)
+    w["chains"] = args.chains
     seeds = [rank * w["chains"] + c for c in range(w["chains"])]
     lat = Lattice(w["L"], seeds, precision="fp32", device=local)
     lat.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
@@ -267,10 +270,11 @@ def main():
         cpu = cpu_oracle_sample()
 
     if rank == 0:
+        wl = WORKLOAD if w["chains"] == WORK["chains"] else WORKLOAD.replace("x 64 chains", f"x {w['chains']} chains")
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "L": L, "M": M, "chains_per_gpu": w["chains"],
+                "config": {"workload": wl, "L": L, "M": M, "chains_per_gpu": w["chains"],
                            "worldlines_per_chain": 2 * Ns, "parallelism": f"chains sharded over {world} GPU(s)",
                            "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2"},
                 "particle_slice_updates_per_s": value * part_slices,
