@@ -54,6 +54,7 @@ typedef struct hqmc_ctx hqmc_ctx;
 #define HQMC_ERR_STATE (-5)       /* call out of order (e.g. sweep before set_params) */
 #define HQMC_ERR_UNSUPPORTED (-6) /* lattice size or mode not built into this library */
 #define HQMC_ERR_NUMERIC (-7)     /* a draw met an all-zero CDF or log Z met a non-positive amplitude */
+#define HQMC_ERR_SCRATCH (-8)     /* the problem does not fit hqmc_ffbs_noalloc's static scratch */
 
 /* Observables of one chain, averaged over slices and over the sweeps accumulated
  * since the last reset (Sec. 4, "Observables").  Per-site quantities. */
@@ -161,6 +162,42 @@ int hqmc_set_profiling(hqmc_ctx *ctx, int max_sweeps);
 /* Sum over the recorded sweeps of the FFBS and the Gibbs/measure device times (ms)
  * and the number of sweeps recorded; clears the record.  Errors: HQMC_ERR_STATE, _CUDA. */
 int hqmc_profile_read(hqmc_ctx *ctx, double *ffbs_ms, double *slice_ms, int *n_sweeps);
+
+/* FFBS of one chain's worldlines that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running inside another framework's memory pool that forbids
+ * untracked device allocations, processes whose device memory is already claimed by a
+ * pre-reserved arena, or loops that must not pay an allocation's implicit device
+ * synchronisation.  It runs the same forward filter and backward sampler as
+ * hqmc_sweep (the FFBS step only: no Gibbs step, no observables) and takes every
+ * intermediate from one static device array of 32 MiB built into the library, which
+ * every device that loads the library keeps until the process exits.
+ *
+ *   L, M, Nsig      lattice size (a built size, L <= 32), slices, worldlines per spin
+ *   t, U, dtau      model parameters as in hqmc_set_params
+ *   seed, sweep     Philox key and sweep index: the call draws exactly what sweep
+ *                   number `sweep` of a context chain with this seed draws in its FFBS
+ *   s               device, [M][N] int8 field (+1/-1), read only
+ *   x               device, [2][Nsig][M] int32 sites, read and overwritten with the new paths
+ *   logw            device, [2][Nsig] double, receives the filter log-weights
+ *   precision       HQMC_FP32 or HQMC_FP64
+ *   stream          cudaStream_t (as void*) the work is ordered on; the call blocks until done
+ *
+ * The caller owns s, x and logw.  Scratch needed: the fixed part (tables, the packed
+ * field, 16-bit worldlines, a [2][M][N] int32 histogram; about 6 B per site-slice plus
+ * 4 B per worldline-slice) plus at least one slot of M*N*8 bytes (16 for FP64); a problem
+ * that does not fit 32 MiB is rejected with HQMC_ERR_SCRATCH.  Fewer slots than pairs
+ * only lowers parallelism.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the one array and each call re-initialises
+ * what must start at zero; calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.
+ * Errors: HQMC_ERR_ARG (null pointers, sizes, or s/x values out of range),
+ * HQMC_ERR_UNSUPPORTED, HQMC_ERR_SCRATCH, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
+int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed,
+                      uint64_t sweep, const int8_t *s, int32_t *x, double *logw, int precision,
+                      void *stream);
 
 /* Lattice sizes built into this library: writes up to cap entries, returns the count. */
 int hqmc_supported_L(int *out, int cap);

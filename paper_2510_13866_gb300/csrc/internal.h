@@ -92,6 +92,7 @@ cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stre
 cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int slices_per_cta,
                          bool measure, cudaStream_t stream);
 cudaError_t configure_slice();
+void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
                            double *sk_out, long long total_N, cudaStream_t stream);

@@ -171,6 +171,24 @@ void build_tab(const HostChain &h, ChainTab &tb, double lam) {
 
 double hirsch_lambda(double U, double dtau) { return std::acosh(std::exp(0.5 * dtau * U)); }
 
+}  // namespace
+
+namespace hqmc {
+// Tables and lambda of one chain, for entry points that do not own a context.
+void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam) {
+    HostChain h;
+    h.L = L;
+    h.N = L * L;
+    h.t = t;
+    h.U = U;
+    h.dtau = dtau;
+    *lam = hirsch_lambda(U, dtau);
+    build_tab(h, tb, *lam);
+}
+}  // namespace hqmc
+
+namespace {
+
 int check_params(hqmc_ctx *c, int L, double t, double U, double beta, double dtau, double filling, int *M,
                  int *Nsig) {
     if (!(t >= 0.0) || !std::isfinite(t)) return fail(c, HQMC_ERR_ARG, "t must be finite and >= 0");
@@ -497,6 +515,7 @@ const char *hqmc_strerror(int code) {
         case HQMC_ERR_STATE: return "call out of order";
         case HQMC_ERR_UNSUPPORTED: return "unsupported lattice size or mode";
         case HQMC_ERR_NUMERIC: return "numerical degeneracy";
+        case HQMC_ERR_SCRATCH: return "problem exceeds the static scratch of hqmc_ffbs_noalloc";
         default: return "unknown error";
     }
 }

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libhqmc.so")
 HQMC_FP32, HQMC_FP64 = 0, 1
 ERRORS = {
     -1: "HQMC_ERR_ARG", -2: "HQMC_ERR_NOMEM", -3: "HQMC_ERR_CUDA", -4: "HQMC_ERR_TIMEOUT",
-    -5: "HQMC_ERR_STATE", -6: "HQMC_ERR_UNSUPPORTED", -7: "HQMC_ERR_NUMERIC",
+    -5: "HQMC_ERR_STATE", -6: "HQMC_ERR_UNSUPPORTED", -7: "HQMC_ERR_NUMERIC", -8: "HQMC_ERR_SCRATCH",
 }
 
 # every entry point declared in include/hqmc.h, with its ctypes signature
@@ -35,6 +35,7 @@ SIGNATURES = {
     "hqmc_set_state": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hqmc_set_profiling": (_i, [_vp, _i]),
     "hqmc_profile_read": (_i, [_vp, _vp, _vp, _vp]),
+    "hqmc_ffbs_noalloc": (_i, [_i, _i, _i, _d, _d, _d, _u64, _u64, _vp, _vp, _vp, _i, _vp]),
     "hqmc_supported_L": (_i, [_vp, _i]),
     "hqmc_destroy": (None, [_vp]),
     "hqmc_strerror": (C.c_char_p, [_i]),

@@ -46,7 +46,7 @@ def test_strerror_and_supported_sizes(libpath):
     from paper_2510_13866_gb300 import hqmc
 
     lib = hqmc.lib()
-    for code in range(-7, 1):
+    for code in range(-8, 1):
         assert lib.hqmc_strerror(code)
     assert 32 in hqmc.supported_L() and 16 in hqmc.supported_L()
 
