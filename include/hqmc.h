@@ -93,7 +93,7 @@ int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
 
 /* Launch configuration: use_graph = replay one captured CUDA graph per sweep;
  * persistent = size the FFBS grid to the resident capacity (each worldline group
- * loops over pairs) instead of one group per pair; warps_per_cta in {1,2,4,8,16}
+ * loops over pairs) instead of one group per pair; warps_per_cta in {1,2,4,8}
  * (0 = default).  Takes effect at the next sweep.  Errors: HQMC_ERR_ARG. */
 int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
 

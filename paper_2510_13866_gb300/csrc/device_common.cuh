@@ -1,32 +1,65 @@
-// device_common.cuh -- register-resident complex FFT of one lattice line, Philox4x64-10,
-// and small warp helpers shared by the sm_103a kernels of this library.
+// device_common.cuh -- two-worldline vector arithmetic, a register-resident complex FFT
+// over those vectors, Philox4x64-10, and small warp helpers shared by the sm_103a kernels
+// of this library.
 #pragma once
 
 #include <cstdint>
 #include <type_traits>
 
+#include <cuda_runtime.h>
+
 namespace hqmc {
 
 // ---------------------------------------------------------------------------------
-// complex value of one lattice line element; .x and .y carry two worldlines of the
-// same spin (the propagator and the slice potential are real, so the two never mix)
+// Two same-spin worldlines travel together through the filter: component .x belongs to
+// one, .y to the other.  The propagator and the slice potential are real, so every
+// operation of the filter acts on both components alike.  In FP32 that is one packed
+// f32x2 instruction (FADD2 / FMUL2 / FFMA2, sm_100 and later) for the pair.
 // ---------------------------------------------------------------------------------
 template <typename T>
-struct cplx {
-    T x, y;
+struct vec2_of;
+template <>
+struct vec2_of<float> {
+    using type = float2;
+};
+template <>
+struct vec2_of<double> {
+    using type = double2;
+};
+template <typename T>
+using vec2_t = typename vec2_of<T>::type;
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsplat(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsplat(double s) { return make_double2(s, s); }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+
+// complex number whose real and imaginary parts are two-worldline vectors
+template <typename V>
+struct cvec {
+    V re, im;
 };
 
-template <typename T>
-__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
-template <typename T>
-__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
-template <typename T>
-__device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
-// multiply by +i or -i
-template <int SGN, typename T>
-__device__ __forceinline__ cplx<T> cmul_i(cplx<T> a) {
-    if constexpr (SGN > 0) return {-a.y, a.x};
-    else return {a.y, -a.x};
+template <typename V>
+__device__ __forceinline__ cvec<V> cv_add(cvec<V> a, cvec<V> b) { return {vadd(a.re, b.re), vadd(a.im, b.im)}; }
+template <typename V>
+__device__ __forceinline__ cvec<V> cv_sub(cvec<V> a, cvec<V> b) { return {vsub(a.re, b.re), vsub(a.im, b.im)}; }
+// multiply by +i (SGN > 0) or -i
+template <int SGN, typename V>
+__device__ __forceinline__ cvec<V> cv_muli(cvec<V> a) {
+    if constexpr (SGN > 0) return {vsub(vzero(a.im), a.im), a.re};
+    else return {a.im, vsub(vzero(a.re), a.re)};
 }
 
 // ---------------------------------------------------------------------------------
@@ -96,51 +129,65 @@ __device__ __forceinline__ void static_for(F &&f) {
     }
 }
 
+template <typename V>
+struct scalar_of;
+template <>
+struct scalar_of<float2> {
+    using type = float;
+};
+template <>
+struct scalar_of<double2> {
+    using type = double;
+};
+
 // v * exp(SGN * 2 pi i K / NN), with the trivial angles done without multiplies
-template <int SGN, int K, int NN, typename T>
-__device__ __forceinline__ cplx<T> twiddle(cplx<T> v) {
+template <int SGN, int K, int NN, typename V>
+__device__ __forceinline__ cvec<V> twiddle(cvec<V> v) {
+    using T = typename scalar_of<V>::type;
     constexpr int k = ((K % NN) + NN) % NN;
     if constexpr (k == 0) {
         return v;
     } else if constexpr (2 * k == NN) {
-        return {-v.x, -v.y};
+        return {vsub(vzero(v.re), v.re), vsub(vzero(v.im), v.im)};
     } else if constexpr (4 * k == NN) {
-        return cmul_i<SGN>(v);
+        return cv_muli<SGN>(v);
     } else if constexpr (4 * k == 3 * NN) {
-        return cmul_i<-SGN>(v);
+        return cv_muli<-SGN>(v);
     } else {
         constexpr T c = T(ct::cos2pi(k, NN));
         constexpr T s = T(SGN * ct::sin2pi(k, NN));
-        return {v.x * c - v.y * s, v.x * s + v.y * c};
+        // (re + i im)(c + i s) = (c re - s im) + i (s re + c im)
+        return {vfma(v.re, vsplat(c), vmul(v.im, vsplat(-s))), vfma(v.re, vsplat(s), vmul(v.im, vsplat(c)))};
     }
 }
 
 // small DFTs of the mixed-radix decomposition (natural order in and out)
-template <int SGN, typename T>
-__device__ __forceinline__ void dft2(cplx<T> &a0, cplx<T> &a1) {
-    cplx<T> t = a0;
-    a0 = cadd(t, a1);
-    a1 = csub(t, a1);
+template <int SGN, typename V>
+__device__ __forceinline__ void dft2(cvec<V> &a0, cvec<V> &a1) {
+    cvec<V> t = a0;
+    a0 = cv_add(t, a1);
+    a1 = cv_sub(t, a1);
 }
-template <int SGN, typename T>
-__device__ __forceinline__ void dft3(cplx<T> &a0, cplx<T> &a1, cplx<T> &a2) {
+template <int SGN, typename V>
+__device__ __forceinline__ void dft3(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2) {
+    using T = typename scalar_of<V>::type;
     constexpr T h = T(-0.5);
     constexpr T s = T(SGN * 0.86602540378443864676372317075293618);
-    cplx<T> sum = cadd(a1, a2), dif = csub(a1, a2);
-    cplx<T> base = {a0.x + h * sum.x, a0.y + h * sum.y};
-    cplx<T> rot = {-s * dif.y, s * dif.x};  // i s (a1 - a2)
-    a0 = cadd(a0, sum);
-    a1 = cadd(base, rot);
-    a2 = csub(base, rot);
+    cvec<V> sum = cv_add(a1, a2), dif = cv_sub(a1, a2);
+    cvec<V> base = {vfma(sum.re, vsplat(h), a0.re), vfma(sum.im, vsplat(h), a0.im)};
+    cvec<V> rot = {vmul(dif.im, vsplat(-s)), vmul(dif.re, vsplat(s))};  // i s (a1 - a2)
+    a0 = cv_add(a0, sum);
+    a1 = cv_add(base, rot);
+    a2 = cv_sub(base, rot);
 }
-template <int SGN, typename T>
-__device__ __forceinline__ void dft4(cplx<T> &a0, cplx<T> &a1, cplx<T> &a2, cplx<T> &a3) {
-    cplx<T> s02 = cadd(a0, a2), d02 = csub(a0, a2);
-    cplx<T> s13 = cadd(a1, a3), d13 = cmul_i<SGN>(csub(a1, a3));
-    a0 = cadd(s02, s13);
-    a2 = csub(s02, s13);
-    a1 = cadd(d02, d13);
-    a3 = csub(d02, d13);
+template <int SGN, typename V>
+__device__ __forceinline__ void dft4(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2, cvec<V> &a3) {
+    cvec<V> s02 = cv_add(a0, a2), d02 = cv_sub(a0, a2);
+    cvec<V> s13 = cv_add(a1, a3), d13 = cv_muli<SGN>(cv_sub(a1, a3));
+    a0 = cv_add(s02, s13);
+    a2 = cv_sub(s02, s13);
+    a1 = cv_add(d02, d13);
+    a3 = cv_sub(d02, d13);
 }
 
 template <int N>
@@ -150,8 +197,8 @@ __host__ __device__ constexpr int first_radix() {
 
 // In-place DFT of N register values, X[k] = sum_n a[n] exp(SGN 2 pi i n k / N),
 // unnormalised, by recursive decimation in time (N = R * Ms, R in {2, 3, 4}).
-template <int N, int SGN, typename T>
-__device__ __forceinline__ void fft(cplx<T> (&a)[N]) {
+template <int N, int SGN, typename V>
+__device__ __forceinline__ void fft(cvec<V> (&a)[N]) {
     if constexpr (N == 1) {
     } else if constexpr (N == 2) {
         dft2<SGN>(a[0], a[1]);
@@ -163,7 +210,7 @@ __device__ __forceinline__ void fft(cplx<T> (&a)[N]) {
         constexpr int R = first_radix<N>();
         constexpr int Ms = N / R;
         static_assert(R * Ms == N, "radix");
-        cplx<T> sub[R][Ms];
+        cvec<V> sub[R][Ms];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -172,7 +219,7 @@ __device__ __forceinline__ void fft(cplx<T> (&a)[N]) {
         for (int r = 0; r < R; ++r) fft<Ms, SGN>(sub[r]);
         static_for<0, Ms>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
-            cplx<T> t[R];
+            cvec<V> t[R];
             t[0] = sub[0][k];
             static_for<1, R>([&](auto RI) {
                 constexpr int r = decltype(RI)::value;
@@ -187,18 +234,62 @@ __device__ __forceinline__ void fft(cplx<T> (&a)[N]) {
     }
 }
 
-// Periodic convolution of one line with the even real kernel whose DFT is gh[k]
-// (gh already divided by N): a <- IDFT(gh . DFT(a)).  gh holds k = 0..N/2.
-template <int N, typename T>
-__device__ __forceinline__ void conv_line(cplx<T> (&a)[N], const T (&gh)[N / 2 + 1]) {
-    fft<N, -1>(a);
+// Periodic convolution of one lattice line of both worldlines with the even real line
+// kernel g: v <- g * v.
+//
+// Even L: the line is packed as n = L/2 complex values z_m = v_{2m} + i v_{2m+1}.  With
+// Z = DFT_n(z), the half-spectrum identities of a real DFT give the packed transform of
+// the convolved line directly as
+//     Z'_k = alpha_k Z_k + i beta_k conj(Z_{(n-k) mod n})
+// with theta_k = 2 pi k / L, P_k = (gh_k + gh_{k+n}) / 2, Q_k = (gh_k - gh_{k+n}) / 2,
+//     alpha_k = (P_k - Q_k sin theta_k) / n,   beta_k = Q_k cos theta_k / n,
+// gh the L-point DFT of g; then z' = IDFT_n(Z') unpacks to the convolved line.  Two
+// half-size complex FFTs per line, all arithmetic on two-worldline vectors.
+// Odd L: full-size complex DFT of the real line, multiply by gh_k / L, inverse DFT.
+// `mix` holds alpha_k, beta_k interleaved (even L) or gh_k / L (odd L).
+template <int L, typename V, typename T>
+__device__ __forceinline__ void conv_line(V (&v)[L], const T *__restrict__ mix) {
+    if constexpr (L % 2 == 0) {
+        constexpr int n = L / 2;
+        cvec<V> z[n];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const T w = gh[k <= N / 2 ? k : N - k];
-        a[k].x *= w;
-        a[k].y *= w;
+        for (int m = 0; m < n; ++m) z[m] = {v[2 * m], v[2 * m + 1]};
+        fft<n, -1>(z);
+        static_for<0, n>([&](auto KI) {
+            constexpr int k = decltype(KI)::value;
+            constexpr int kp = (n - k) % n;
+            if constexpr (k == kp) {
+                const V al = vsplat(mix[2 * k]), be = vsplat(mix[2 * k + 1]);
+                const cvec<V> zk = z[k];
+                z[k] = {vfma(zk.re, al, vmul(zk.im, be)), vfma(zk.im, al, vmul(zk.re, be))};
+            } else if constexpr (k < kp) {
+                const V a0 = vsplat(mix[2 * k]), b0 = vsplat(mix[2 * k + 1]);
+                const V a1 = vsplat(mix[2 * kp]), b1 = vsplat(mix[2 * kp + 1]);
+                const cvec<V> zk = z[k], zp = z[kp];
+                z[k] = {vfma(zk.re, a0, vmul(zp.im, b0)), vfma(zk.im, a0, vmul(zp.re, b0))};
+                z[kp] = {vfma(zp.re, a1, vmul(zk.im, b1)), vfma(zp.im, a1, vmul(zk.re, b1))};
+            }
+        });
+        fft<n, +1>(z);
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+            v[2 * m] = z[m].re;
+            v[2 * m + 1] = z[m].im;
+        }
+    } else {
+        cvec<V> z[L];
+#pragma unroll
+        for (int m = 0; m < L; ++m) z[m] = {v[m], vzero(v[m])};
+        fft<L, -1>(z);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const V w = vsplat(mix[k]);
+            z[k] = {vmul(z[k].re, w), vmul(z[k].im, w)};
+        }
+        fft<L, +1>(z);
+#pragma unroll
+        for (int m = 0; m < L; ++m) v[m] = z[m].re;
     }
-    fft<N, +1>(a);
 }
 
 // ---------------------------------------------------------------------------------
@@ -256,5 +347,17 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
     for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
     return v;
 }
+
+// Ampere-style asynchronous global -> shared copies (16 or 8 bytes per lane).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 }  // namespace hqmc

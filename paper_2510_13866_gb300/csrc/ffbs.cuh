@@ -1,18 +1,21 @@
 // ffbs.cuh -- forward-filtering backward-sampling of worldline pairs (Sec. 3.5.2).
 //
-// A group of L lanes (L <= 32) owns one pair of same-spin worldlines of one chain;
-// the two are the real and imaginary parts of one complex L x L array, since the
-// propagator G and the slice potential W are real (they never mix the parts).
-// Each lane holds one lattice line in registers.  One slice of the forward filter
+// A group of GW >= L lanes owns one pair of same-spin worldlines of one chain; the two
+// travel together as the .x/.y components of a two-worldline vector (FP32: one packed
+// f32x2 instruction per operation on the pair).  Each lane holds one lattice line in
+// registers.  One slice of the forward filter
 //     alpha_{l+1} = G * (W_l . alpha_l)            (Eq. ffbsFwd, position basis)
-// is a line convolution along the in-register direction (FFT, multiply by the 1D
-// kernel g^, inverse FFT), one transpose through shared memory, and the same along
-// the other direction: G = g (x) g is separable, so the layout simply alternates
-// between slices and only one transpose per slice is needed.  The message is
-// renormalised by an exact power of two after every slice; the exponents are summed
-// as integers, so the running log-normaliser is exact and log Z is formed in FP64.
-// f_l = W_l . alpha_l is written to a per-group scratch slot (column-major), and the
-// backward pass reads it back slice by slice to draw
+// is a line convolution along the in-register direction, one transpose through shared
+// memory, and the same along the other direction: G = g (x) g is separable, so the
+// layout simply alternates between slices and one transpose per slice suffices.  A line
+// convolution of the real lines is two half-length complex FFTs with a pairwise
+// spectral mix between them (conv_line in device_common.cuh).  The message is
+// renormalised by an exact power of two after every slice; the exponents are summed as
+// integers, so the running log-normaliser is exact and log Z is formed in FP64.
+//
+// f_l = W_l . alpha_l is streamed to a per-group scratch slot with coalesced 16-byte
+// stores.  The backward pass prefetches each slice into shared memory with asynchronous
+// copies while the previous slice is being sampled, and draws
 //     x_l ~ max(f_l(y), 0) G(x_{l+1} - y)
 // by the row-major inverse CDF with a Philox uniform, fusing the occupancy histogram
 // and the kinetic-energy link sum.
@@ -23,12 +26,22 @@
 
 namespace hqmc {
 
-template <int L>
+template <typename T, int L>
 struct FfbsGeo {
     static_assert(L >= 2 && L <= 32, "register-line FFBS covers L <= 32");
+    using V = vec2_t<T>;
     static constexpr int GW = (L <= 4) ? 4 : (L <= 8) ? 8 : (L <= 16) ? 16 : 32;  // lanes per group
     static constexpr int GPW = 32 / GW;                                          // groups per warp
-    static constexpr int BUF = L * (L + 1);  // transpose buffer (padded rows), complex elements
+    // elements per 16-byte chunk of the f slot (odd L in FP32: 8-byte chunks of one element)
+    static constexpr int CH = (sizeof(T) == 4 && L % 2 == 0) ? 2 : 1;
+    static constexpr int CHB = CH * int(sizeof(V));                                // chunk bytes
+    static constexpr int LP = L + CH;                                              // transpose pitch
+    static constexpr size_t XBUF = size_t(L) * LP * sizeof(V);
+    static constexpr size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
+    static constexpr size_t MIXB = a16(size_t(L) * sizeof(T));
+    static constexpr size_t G2B = a16(size_t(2 * L) * sizeof(T));
+    static constexpr size_t WXB = a16(size_t(L) * sizeof(V));
+    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB;
 };
 
 // comparison value for "u*S < C(y)" when C is held in T: round u*S down to T,
@@ -41,11 +54,11 @@ template <>
 __device__ __forceinline__ double cmp_value<double>(double t) { return t; }
 
 template <typename T>
-__device__ __forceinline__ const T *tab_ghat(const ChainTab &tb);
+__device__ __forceinline__ const T *tab_mix(const ChainTab &tb);
 template <>
-__device__ __forceinline__ const float *tab_ghat<float>(const ChainTab &tb) { return tb.ghat_f; }
+__device__ __forceinline__ const float *tab_mix<float>(const ChainTab &tb) { return tb.mix_f; }
 template <>
-__device__ __forceinline__ const double *tab_ghat<double>(const ChainTab &tb) { return tb.ghat_d; }
+__device__ __forceinline__ const double *tab_mix<double>(const ChainTab &tb) { return tb.mix_d; }
 template <typename T>
 __device__ __forceinline__ const T *tab_g(const ChainTab &tb);
 template <>
@@ -54,20 +67,44 @@ template <>
 __device__ __forceinline__ const double *tab_g<double>(const ChainTab &tb) { return tb.g_d; }
 
 // pick element r of a register array with a runtime index (no local-memory spill)
-template <int L, typename T>
-__device__ __forceinline__ cplx<T> reg_select(const cplx<T> (&v)[L], int r) {
-    cplx<T> o = v[0];
+template <int L, typename V>
+__device__ __forceinline__ V reg_select(const V (&v)[L], int r) {
+    V o = v[0];
 #pragma unroll
     for (int k = 1; k < L; ++k)
         if (k == r) o = v[k];
     return o;
 }
 
+template <typename V>
+__device__ __forceinline__ V vmax0(V a) {
+    return {a.x > 0 ? a.x : decltype(a.x)(0), a.y > 0 ? a.y : decltype(a.y)(0)};
+}
+
+// chunk c of an f slot (CH consecutive elements of one writer lane)
 template <typename T, int L>
-__global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
-    using G = FfbsGeo<L>;
+__device__ __forceinline__ void store_chunk(vec2_t<T> *dst, int c, const vec2_t<T> *e) {
+    using G = FfbsGeo<T, L>;
+    if constexpr (G::CH == 2) {
+        reinterpret_cast<float4 *>(dst)[c] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+    } else {
+        dst[c] = e[0];
+    }
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_t<T> *gsrc, int gc) {
+    using G = FfbsGeo<T, L>;
+    if constexpr (G::CHB == 16) cp_async16(sdst + size_t(sc) * G::CH, gsrc + size_t(gc) * G::CH);
+    else cp_async8(sdst + sc, gsrc + gc);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevState st, FfbsLaunch fl) {
+    using G = FfbsGeo<T, L>;
+    using V = vec2_t<T>;
     constexpr int N = L * L;
-    constexpr int GW = G::GW;
+    constexpr int GW = G::GW, CH = G::CH, LP = G::LP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -76,10 +113,14 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
     const unsigned gmask = (GW == 32) ? 0xffffffffu : (((1u << GW) - 1u) << (gw * GW));
     const bool active = gl < L;
     const int wpc = blockDim.x >> 5;
-    cplx<T> *buf = reinterpret_cast<cplx<T> *>(smem_raw) + (warp * G::GPW + gw) * G::BUF;
+    unsigned char *gsm = smem_raw + size_t(warp * G::GPW + gw) * G::GROUP_BYTES;
+    V *xbuf = reinterpret_cast<V *>(gsm);
+    T *mix = reinterpret_cast<T *>(gsm + G::XBUF);
+    T *g2 = reinterpret_cast<T *>(gsm + G::XBUF + G::MIXB);
+    V *wx = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B);
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
     const long long ngroups = (long long)gridDim.x * wpc * G::GPW;
-    cplx<T> *slot = reinterpret_cast<cplx<T> *>(fl.scratch) + gid * fl.slot_elems;
+    V *slot = reinterpret_cast<V *>(fl.scratch) + gid * fl.slot_elems;
     const uint64_t sweep = *st.sweep;
 
     for (long long q = gid; q < fl.total_pairs; q += ngroups) {
@@ -105,13 +146,15 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
         int16_t *xp0 = st.x + cd.x_off + (long long)wl0 * M;
         int16_t *xp1 = st.x + cd.x_off + (long long)wl1 * M;
 
-        // 1D kernel in k-space (already divided by L), k = 0..L/2
-        T gh[L / 2 + 1];
+        // line-convolution constants and the doubled real-space kernel g2[j] = g(j mod L)
+        __syncwarp(gmask);
         {
-            const T *src = tab_ghat<T>(tb);
-#pragma unroll
-            for (int k = 0; k <= L / 2; ++k) gh[k] = src[k];
+            const T *src = tab_mix<T>(tb);
+            for (int j = gl; j < L; j += GW) mix[j] = src[j];
+            const T *gs = tab_g<T>(tb);
+            for (int j = gl; j < 2 * L; j += GW) g2[j] = gs[j < L ? j : j - L];
         }
+        __syncwarp(gmask);
 
         // ---- anchor slice (phase 2) ----
         const u64x4 ua = philox4x64_10(0, 0, 2, sweep, cd.seed, 0);
@@ -123,7 +166,7 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
         const int ax0 = xa0 % L, ay0 = xa0 / L, ax1 = xa1 % L, ay1 = xa1 / L;
 
         // ---- forward filter ----
-        cplx<T> v[L];
+        V v[L];
         {
             // f_a = W_a(x_a) delta_{x_a}, layout R: lane = iy, register = ix
             const uint32_t w = active ? srow[((long long)a * L + gl) * cd.wpl] : 0u;
@@ -138,40 +181,47 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
         T fin0 = T(0), fin1 = T(0);
         int l = a;
         for (int i = 0; i < M; ++i) {
-            const bool layC = (i & 1) != 0;  // layout of f_l: R (lane = iy) or C (lane = ix)
+            // f_l of slice i, in the writer's layout: chunk j*L + lane holds registers CH*j..
             if (i >= 1 && active) {
-                cplx<T> *dst = slot + (long long)i * N;
-                if (!layC) {
+                V *dst = slot + (long long)i * N;
 #pragma unroll
-                    for (int r = 0; r < L; ++r) dst[r * L + gl] = v[r];
-                } else {
+                for (int j = 0; j < L / CH; ++j) store_chunk<T, L>(dst, j * L + gl, &v[CH * j]);
+            }
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                conv_line<L>(v, mix);
+                if (h == 0) {
+                    // transpose: lane p, register r  ->  lane r, register p
+                    __syncwarp(gmask);
+                    if (active) {
 #pragma unroll
-                    for (int r = 0; r < L; ++r) dst[gl * L + r] = v[r];
+                        for (int r = 0; r < L; ++r) xbuf[r * LP + gl] = v[r];
+                    }
+                    __syncwarp(gmask);
+                    if (active) {
+                        const V *src = xbuf + gl * LP;
+                        if constexpr (CH == 2) {
+#pragma unroll
+                            for (int j = 0; j < L / 2; ++j) {
+                                const float4 c4 = reinterpret_cast<const float4 *>(src)[j];
+                                v[2 * j] = make_float2(c4.x, c4.y);
+                                v[2 * j + 1] = make_float2(c4.z, c4.w);
+                            }
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < L; ++p) v[p] = src[p];
+                        }
+                    }
                 }
             }
-            conv_line<L, T>(v, gh);
-            __syncwarp(gmask);
-            if (active) {
-#pragma unroll
-                for (int r = 0; r < L; ++r) buf[r * (L + 1) + gl] = v[r];
-            }
-            __syncwarp(gmask);
-            if (active) {
-#pragma unroll
-                for (int r = 0; r < L; ++r) v[r] = buf[gl * (L + 1) + r];
-            }
-            conv_line<L, T>(v, gh);
             // v = alpha_{l+1} (scale 2^{-esum}) in the other layout
-            T s0 = T(0), s1 = T(0);
+            V s = vzero(v[0]);
             if (active) {
 #pragma unroll
-                for (int r = 0; r < L; ++r) {
-                    s0 += v[r].x;
-                    s1 += v[r].y;
-                }
+                for (int r = 0; r < L; ++r) s = vadd(s, v[r]);
             }
-            s0 = group_sum<GW>(s0, gmask);
-            s1 = group_sum<GW>(s1, gmask);
+            T s0 = group_sum<GW>(s.x, gmask);
+            T s1 = group_sum<GW>(s.y, gmask);
             const int l1 = (l + 1 == M) ? 0 : l + 1;
             if (i < M - 1) {
                 int e0 = 0, e1 = 0;
@@ -181,23 +231,19 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
                 esum0 += e0;
                 esum1 += e1;
                 const T sc0 = fbits<T>::pow2(-e0), sc1 = fbits<T>::pow2(-e1);
-                const T a0 = wp * sc0, b0 = wm * sc0, a1 = wp * sc1, b1 = wm * sc1;
-                // new layout is C (lane = ix) when i is even
-                const uint32_t *wsrc = layC ? srow : scol;
+                const V A = {wp * sc0, wp * sc1}, B = {wm * sc0, wm * sc1};
+                // the new layout is C (lane = ix) when i is even: bits by columns
+                const uint32_t *wsrc = (i & 1) ? srow : scol;
                 const uint32_t w = active ? wsrc[((long long)l1 * L + gl) * cd.wpl] : 0u;
 #pragma unroll
-                for (int r = 0; r < L; ++r) {
-                    const bool up = (w >> r) & 1u;
-                    v[r].x *= up ? a0 : b0;
-                    v[r].y *= up ? a1 : b1;
-                }
+                for (int r = 0; r < L; ++r) v[r] = vmul(v[r], ((w >> r) & 1u) ? A : B);
             } else {
                 // alpha_M(x_a): final layout is C if M is odd
                 const bool finC = (M & 1) != 0;
                 const int own0 = finC ? ax0 : ay0, reg0 = finC ? ay0 : ax0;
                 const int own1 = finC ? ax1 : ay1, reg1 = finC ? ay1 : ax1;
-                const T c0 = reg_select<L, T>(v, reg0).x;
-                const T c1 = reg_select<L, T>(v, reg1).y;
+                const T c0 = reg_select<L>(v, reg0).x;
+                const T c1 = reg_select<L>(v, reg1).y;
                 fin0 = __shfl_sync(gmask, c0, own0, GW);
                 fin1 = __shfl_sync(gmask, c1, own1, GW);
             }
@@ -215,14 +261,19 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
         }
 
         // ---- backward sampling ----
-        // doubled real-space table g2[j] = g(j mod L), j in [0, 2L), in this group's buffer
+        // slice i of the slot -> xbuf: R slices (i even) chunk-for-chunk, C slices (i odd)
+        // into rows of pitch L+1 chunks so that the row-wise reads below are conflict-free
+        auto prefetch = [&](int i) {
+            if (active) {
+                const V *src = slot + (long long)i * N;
+                const int pitch = (i & 1) ? L + 1 : L;
+#pragma unroll
+                for (int j = 0; j < L / CH; ++j) async_chunk<T, L>(xbuf, j * pitch + gl, src, j * L + gl);
+            }
+            cp_async_commit();
+        };
         __syncwarp(gmask);
-        T *g2 = reinterpret_cast<T *>(buf);
-        {
-            const T *src = tab_g<T>(tb);
-            for (int j = gl; j < 2 * L; j += GW) g2[j] = src[j < L ? j : j - L];
-        }
-        __syncwarp(gmask);
+        if (M > 1) prefetch(M - 1);
         const float *hl = tb.h_f;
         int cur0 = xa0, cur1 = xa1;
         float ek0 = 0.f, ek1 = 0.f;
@@ -232,44 +283,65 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
             if (has1) atomicAdd(hist_s + (long long)a * N + xa1, 1);
         }
         int cached = -1;
-        uint64_t words[4] = {0, 0, 0, 0};
+        uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
         for (int i = M - 1; i >= 1; --i) {
             int lb = a + i;
             if (lb >= M) lb -= M;
+            // row gl of f_l (lane = iy, register = ix)
+            cp_async_wait_all();
+            __syncwarp(gmask);
+            if (active) {
+                if ((i & 1) == 0) {
+#pragma unroll
+                    for (int j = 0; j < L / CH; ++j) {
+                        if constexpr (CH == 2) {
+                            const float4 c4 = reinterpret_cast<const float4 *>(xbuf)[j * L + gl];
+                            v[2 * j] = make_float2(c4.x, c4.y);
+                            v[2 * j + 1] = make_float2(c4.z, c4.w);
+                        } else {
+                            v[j] = xbuf[j * L + gl];
+                        }
+                    }
+                } else {
+                    const V *src = xbuf + (gl / CH) * (L + 1) * CH + gl % CH;
+#pragma unroll
+                    for (int ix = 0; ix < L; ++ix) v[ix] = src[ix * CH];
+                }
+            }
+            __syncwarp(gmask);
+            if (i > 1) prefetch(i - 1);
+
             // uniforms of this slice for both worldlines (lanes 0 and 1 compute, then share)
             const int grp = lb >> 2;
             if (grp != cached) {
                 const u64x4 w4 = philox4x64_10((uint64_t)grp, (gl & 1) ? wl1 : wl0, 0, sweep, cd.seed, 0);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) words[k] = w4.v[k];
+                wd0 = w4.v[0];
+                wd1 = w4.v[1];
+                wd2 = w4.v[2];
+                wd3 = w4.v[3];
                 cached = grp;
             }
-            uint64_t myw = words[0];
-#pragma unroll
-            for (int k = 1; k < 4; ++k)
-                if ((lb & 3) == k) myw = words[k];
+            const int wsel = lb & 3;
+            const uint64_t myw = wsel == 0 ? wd0 : wsel == 1 ? wd1 : wsel == 2 ? wd2 : wd3;
             const double u0 = u53(__shfl_sync(gmask, myw, 0, GW));
             const double u1 = u53(__shfl_sync(gmask, myw, 1, GW));
 
-            // f_l row gl (lane = iy), p(y) = max(f, 0) G(x_{l+1} - y), in-lane prefix
-            const cplx<T> *srcf = slot + (long long)i * N;
+            // p(y) = max(f, 0) g(ix - cx) g(iy - cy): x-weights shared through wx
             const int cx0 = cur0 % L, cy0 = cur0 / L, cx1 = cur1 % L, cy1 = cur1 / L;
-            T rt0 = T(0), rt1 = T(0);
+            if (active) wx[gl] = V{g2[gl - cx0 + L], g2[gl - cx1 + L]};
+            __syncwarp(gmask);
+            V gy = vzero(v[0]);
+            if (active) gy = V{g2[gl - cy0 + L], g2[gl - cy1 + L]};
+            V P = vzero(v[0]);
             if (active) {
-                const T gy0 = g2[gl - cy0 + L], gy1 = g2[gl - cy1 + L];
 #pragma unroll
                 for (int ix = 0; ix < L; ++ix) {
-                    const cplx<T> f = srcf[ix * L + gl];
-                    const T q0 = (f.x > T(0) ? f.x : T(0)) * (gy0 * g2[ix - cx0 + L]);
-                    const T q1 = (f.y > T(0) ? f.y : T(0)) * (gy1 * g2[ix - cx1 + L]);
-                    rt0 += q0;
-                    rt1 += q1;
-                    v[ix].x = rt0;  // inclusive in-row prefix
-                    v[ix].y = rt1;
+                    P = vfma(vmax0(v[ix]), vmul(wx[ix], gy), P);
+                    v[ix] = P;  // inclusive in-row prefix
                 }
             }
             // inclusive scan of row totals over the group's lanes
-            T in0 = rt0, in1 = rt1;
+            T in0 = P.x, in1 = P.y;
 #pragma unroll
             for (int o = 1; o < GW; o <<= 1) {
                 const T t0 = __shfl_up_sync(gmask, in0, o, GW);
@@ -288,46 +360,52 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
             const T S1 = __shfl_sync(gmask, in1, L - 1, GW);
             const T t0 = cmp_value<T>(u0 * double(S0));
             const T t1 = cmp_value<T>(u1 * double(S1));
-            // first site of this row with t < ex + prefix and a positive increment
-            int cand0 = -1, last0 = -1, cand1 = -1, last1 = -1;
+            // the row that holds the crossing, then the first column whose prefix crosses:
+            // the count of prefixes at or below the lane's remaining threshold
+            const T r0 = t0 - ex0, r1 = t1 - ex1;
+            int n0 = 0, n1 = 0;
             if (active) {
-                T pv0 = T(0), pv1 = T(0);
 #pragma unroll
                 for (int ix = 0; ix < L; ++ix) {
-                    const bool inc0 = v[ix].x > pv0, inc1 = v[ix].y > pv1;
-                    if (inc0) {
-                        last0 = ix;
-                        if (cand0 < 0 && t0 < ex0 + v[ix].x) cand0 = ix;
-                    }
-                    if (inc1) {
-                        last1 = ix;
-                        if (cand1 < 0 && t1 < ex1 + v[ix].y) cand1 = ix;
-                    }
-                    pv0 = v[ix].x;
-                    pv1 = v[ix].y;
+                    n0 += (v[ix].x <= r0) ? 1 : 0;
+                    n1 += (v[ix].y <= r1) ? 1 : 0;
                 }
             }
             int nxt0, nxt1;
             {
-                const unsigned b0 = __ballot_sync(gmask, cand0 >= 0) & gmask;
-                const unsigned b1 = __ballot_sync(gmask, cand1 >= 0) & gmask;
-                const unsigned f0 = __ballot_sync(gmask, last0 >= 0) & gmask;
-                const unsigned f1 = __ballot_sync(gmask, last1 >= 0) & gmask;
                 const int base = gw * GW;
-                int row0, row1, col0, col1;
-                if (b0) {
-                    row0 = __ffs(b0) - 1 - base;
-                    col0 = __shfl_sync(gmask, cand0, row0, GW);
-                } else {
-                    row0 = f0 ? 31 - __clz(f0) - base : -1;
-                    col0 = row0 >= 0 ? __shfl_sync(gmask, last0, row0 < 0 ? 0 : row0, GW) : -1;
-                }
-                if (b1) {
-                    row1 = __ffs(b1) - 1 - base;
-                    col1 = __shfl_sync(gmask, cand1, row1, GW);
-                } else {
-                    row1 = f1 ? 31 - __clz(f1) - base : -1;
-                    col1 = row1 >= 0 ? __shfl_sync(gmask, last1, row1 < 0 ? 0 : row1, GW) : -1;
+                const unsigned b0 = __ballot_sync(gmask, active && t0 >= ex0 && n0 < L) & gmask;
+                const unsigned b1 = __ballot_sync(gmask, active && t1 >= ex1 && n1 < L) & gmask;
+                int row0 = b0 ? __ffs(b0) - 1 - base : -1;
+                int row1 = b1 ? __ffs(b1) - 1 - base : -1;
+                int col0 = __shfl_sync(gmask, n0, row0 < 0 ? 0 : row0, GW);
+                int col1 = __shfl_sync(gmask, n1, row1 < 0 ? 0 : row1, GW);
+                if (row0 < 0 || row1 < 0) {
+                    // u*S at or beyond the rounded total: the last site with a positive weight
+                    int last0 = -1, last1 = -1;
+                    if (active) {
+                        V pv = vzero(v[0]);
+#pragma unroll
+                        for (int ix = 0; ix < L; ++ix) {
+                            if (v[ix].x > pv.x) last0 = ix;
+                            if (v[ix].y > pv.y) last1 = ix;
+                            pv = v[ix];
+                        }
+                    }
+                    const unsigned f0 = __ballot_sync(gmask, last0 >= 0) & gmask;
+                    const unsigned f1 = __ballot_sync(gmask, last1 >= 0) & gmask;
+                    const int lr0 = f0 ? 31 - __clz(f0) - base : -1;
+                    const int lr1 = f1 ? 31 - __clz(f1) - base : -1;
+                    const int lc0 = __shfl_sync(gmask, last0, lr0 < 0 ? 0 : lr0, GW);
+                    const int lc1 = __shfl_sync(gmask, last1, lr1 < 0 ? 0 : lr1, GW);
+                    if (row0 < 0) {
+                        row0 = lr0;
+                        col0 = lc0;
+                    }
+                    if (row1 < 0) {
+                        row1 = lr1;
+                        col1 = lc1;
+                    }
                 }
                 if (row0 < 0 || !(S0 > T(0))) {
                     nxt0 = cur0;  // all-zero CDF: stay and report
@@ -368,8 +446,8 @@ __global__ void ffbs_kernel(DevState st, FfbsLaunch fl) {
 
 template <typename T, int L>
 size_t ffbs_smem_bytes_t(int warps_per_cta) {
-    using G = FfbsGeo<L>;
-    return size_t(warps_per_cta) * G::GPW * G::BUF * sizeof(cplx<T>);
+    using G = FfbsGeo<T, L>;
+    return size_t(warps_per_cta) * G::GPW * G::GROUP_BYTES;
 }
 
 }  // namespace hqmc

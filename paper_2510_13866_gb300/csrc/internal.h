@@ -21,6 +21,10 @@ struct ChainTab {
     float h_f[kMaxL];
     double dghat_d[kMaxL]; // d/dt ghat(k)
     float dghat_f[kMaxL];
+    // line-convolution constants of the half-length real FFT (even L): alpha_k, beta_k
+    // interleaved for k = 0..L/2-1; odd L: ghat(k) for k = 0..L-1
+    double mix_d[kMaxL];
+    float mix_f[kMaxL];
     double pplus[2 * kPTab + 1];  // 1 / (1 + e^{-2 lambda m}), m = -kPTab..kPTab
 };
 

@@ -155,6 +155,21 @@ void build_tab(const HostChain &h, ChainTab &tb, double lam) {
         tb.dghat_d[k] = 2.0 * h.dtau * ck * gh / L;
         tb.dghat_f[k] = float(tb.dghat_d[k]);
     }
+    // spectral mix of conv_line: with n = L/2, P = (gh_k + gh_{k+n})/2, Q = (gh_k - gh_{k+n})/2,
+    // alpha_k = (P - Q sin(2 pi k/L)) / n and beta_k = Q cos(2 pi k/L) / n (gh unnormalised)
+    if (L % 2 == 0) {
+        const int n = L / 2;
+        for (int k = 0; k < n; ++k) {
+            const double th = two_pi * k / L;
+            const double ga = std::exp(2.0 * z * std::cos(th)), gb = std::exp(2.0 * z * std::cos(th + 0.5 * two_pi));
+            const double P = 0.5 * (ga + gb), Q = 0.5 * (ga - gb);
+            tb.mix_d[2 * k] = (P - Q * std::sin(th)) / n;
+            tb.mix_d[2 * k + 1] = Q * std::cos(th) / n;
+        }
+    } else {
+        for (int k = 0; k < L; ++k) tb.mix_d[k] = std::exp(2.0 * z * std::cos(two_pi * k / L)) / L;
+    }
+    for (int k = 0; k < L; ++k) tb.mix_f[k] = float(tb.mix_d[k]);
     std::vector<double> g;
     ring_propagator(L, z, g);
     for (int d = 0; d < L; ++d) {
@@ -630,9 +645,8 @@ int hqmc_set_stream(hqmc_ctx *c, void *stream) {
 
 int hqmc_set_launch(hqmc_ctx *c, int use_graph, int persistent, int warps_per_cta) {
     if (!c) return HQMC_ERR_ARG;
-    if (warps_per_cta != 0 && warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8 &&
-        warps_per_cta != 16)
-        return fail(c, HQMC_ERR_ARG, "warps_per_cta must be 0, 1, 2, 4, 8 or 16");
+    if (warps_per_cta != 0 && warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
+        return fail(c, HQMC_ERR_ARG, "warps_per_cta must be 0, 1, 2, 4 or 8");
     const bool relayout = (bool(persistent) != c->persistent) || (warps_per_cta != c->wpc);
     c->use_graph = use_graph != 0;
     c->persistent = persistent != 0;
