@@ -29,10 +29,17 @@ struct vec2_of<double> {
 template <typename T>
 using vec2_t = typename vec2_of<T>::type;
 
+// packed FP32 pair arithmetic (FADD2 / FMUL2 / FFMA2; subtraction as PTX sub.rn.f32x2)
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+    unsigned long long r;
+    const unsigned long long x = *reinterpret_cast<const unsigned long long *>(&a);
+    const unsigned long long y = *reinterpret_cast<const unsigned long long *>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2 *>(&r);
+}
 __device__ __forceinline__ float2 vsplat(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
 
@@ -44,6 +51,25 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
 }
 __device__ __forceinline__ double2 vsplat(double s) { return make_double2(s, s); }
 __device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+
+// (alpha_k, beta_k) broadcast pairs of conv_line's spectral mix, read from shared memory
+// at every use (a volatile load: kept out of registers across the slice loop, where
+// they would cost L registers)
+__device__ __forceinline__ void load_mix(const float2 *mix, int k, float2 &al, float2 &be) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(mix + 2 * k));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(al.x), "=f"(al.y), "=f"(be.x), "=f"(be.y) : "r"(a));
+}
+__device__ __forceinline__ void load_mix(const double2 *mix, int k, double2 &al, double2 &be) {
+    al = mix[2 * k];
+    be = mix[2 * k + 1];
+}
+__device__ __forceinline__ float2 load_mix1(const float2 *mix, int k) {
+    const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(mix + k));
+    float2 r;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(a));
+    return r;
+}
+__device__ __forceinline__ double2 load_mix1(const double2 *mix, int k) { return mix[k]; }
 
 // complex number whose real and imaginary parts are two-worldline vectors
 template <typename V>
@@ -182,12 +208,18 @@ __device__ __forceinline__ void dft3(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2) {
 }
 template <int SGN, typename V>
 __device__ __forceinline__ void dft4(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2, cvec<V> &a3) {
-    cvec<V> s02 = cv_add(a0, a2), d02 = cv_sub(a0, a2);
-    cvec<V> s13 = cv_add(a1, a3), d13 = cv_muli<SGN>(cv_sub(a1, a3));
+    const cvec<V> s02 = cv_add(a0, a2), d02 = cv_sub(a0, a2);
+    const cvec<V> s13 = cv_add(a1, a3), d13 = cv_sub(a1, a3);
     a0 = cv_add(s02, s13);
     a2 = cv_sub(s02, s13);
-    a1 = cv_add(d02, d13);
-    a3 = cv_sub(d02, d13);
+    // a1 = d02 + (SGN i) d13, a3 = d02 - (SGN i) d13, with the rotation folded into add/sub
+    if constexpr (SGN > 0) {
+        a1 = {vsub(d02.re, d13.im), vadd(d02.im, d13.re)};
+        a3 = {vadd(d02.re, d13.im), vsub(d02.im, d13.re)};
+    } else {
+        a1 = {vadd(d02.re, d13.im), vsub(d02.im, d13.re)};
+        a3 = {vsub(d02.re, d13.im), vadd(d02.im, d13.re)};
+    }
 }
 
 template <int N>
@@ -246,9 +278,10 @@ __device__ __forceinline__ void fft(cvec<V> (&a)[N]) {
 // gh the L-point DFT of g; then z' = IDFT_n(Z') unpacks to the convolved line.  Two
 // half-size complex FFTs per line, all arithmetic on two-worldline vectors.
 // Odd L: full-size complex DFT of the real line, multiply by gh_k / L, inverse DFT.
-// `mix` holds alpha_k, beta_k interleaved (even L) or gh_k / L (odd L).
-template <int L, typename V, typename T>
-__device__ __forceinline__ void conv_line(V (&v)[L], const T *__restrict__ mix) {
+// `mix` holds alpha_k, beta_k interleaved (even L) or gh_k / L (odd L), each already
+// broadcast to both components.
+template <int L, typename V>
+__device__ __forceinline__ void conv_line(V (&v)[L], const V *mix) {
     if constexpr (L % 2 == 0) {
         constexpr int n = L / 2;
         cvec<V> z[n];
@@ -259,12 +292,14 @@ __device__ __forceinline__ void conv_line(V (&v)[L], const T *__restrict__ mix) 
             constexpr int k = decltype(KI)::value;
             constexpr int kp = (n - k) % n;
             if constexpr (k == kp) {
-                const V al = vsplat(mix[2 * k]), be = vsplat(mix[2 * k + 1]);
+                V al, be;
+                load_mix(mix, k, al, be);
                 const cvec<V> zk = z[k];
                 z[k] = {vfma(zk.re, al, vmul(zk.im, be)), vfma(zk.im, al, vmul(zk.re, be))};
             } else if constexpr (k < kp) {
-                const V a0 = vsplat(mix[2 * k]), b0 = vsplat(mix[2 * k + 1]);
-                const V a1 = vsplat(mix[2 * kp]), b1 = vsplat(mix[2 * kp + 1]);
+                V a0, b0, a1, b1;
+                load_mix(mix, k, a0, b0);
+                load_mix(mix, kp, a1, b1);
                 const cvec<V> zk = z[k], zp = z[kp];
                 z[k] = {vfma(zk.re, a0, vmul(zp.im, b0)), vfma(zk.im, a0, vmul(zp.re, b0))};
                 z[kp] = {vfma(zp.re, a1, vmul(zk.im, b1)), vfma(zp.im, a1, vmul(zk.re, b1))};
@@ -283,7 +318,7 @@ __device__ __forceinline__ void conv_line(V (&v)[L], const T *__restrict__ mix) 
         fft<L, -1>(z);
 #pragma unroll
         for (int k = 0; k < L; ++k) {
-            const V w = vsplat(mix[k]);
+            const V w = load_mix1(mix, k);
             z[k] = {vmul(z[k].re, w), vmul(z[k].im, w)};
         }
         fft<L, +1>(z);

@@ -38,20 +38,26 @@ struct FfbsGeo {
     static constexpr int LP = L + CH;                                              // transpose pitch
     static constexpr size_t XBUF = size_t(L) * LP * sizeof(V);
     static constexpr size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
-    static constexpr size_t MIXB = a16(size_t(L) * sizeof(T));
+    static constexpr size_t MIXB = a16(size_t(L) * sizeof(V));
     static constexpr size_t G2B = a16(size_t(2 * L) * sizeof(T));
     static constexpr size_t WXB = a16(size_t(L) * sizeof(V));
     static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB;
 };
 
-// comparison value for "u*S < C(y)" when C is held in T: round u*S down to T,
-// so that  t < C  <=>  rd(t) < C  for every C representable in T.
+// Target u*S of an inverse-CDF draw from the Philox word w, in the CDF's precision.
+// FP64: u = (w >> 11) 2^-53 and t = u*S.  FP32: u truncated to its leading 24 fraction
+// bits, u24 = (w >> 40) 2^-24 (exact in FP32, |u - u24| < 2^-24), and t = u24*S rounded
+// down, so no FP64 instruction enters the per-slice loop; the perturbation of u is far
+// below the draw tolerance of the FP32 path.
 template <typename T>
-__device__ __forceinline__ T cmp_value(double t);
+__device__ __forceinline__ T draw_target(uint64_t w, T S);
 template <>
-__device__ __forceinline__ float cmp_value<float>(double t) { return __double2float_rd(t); }
+__device__ __forceinline__ float draw_target<float>(uint64_t w, float S) {
+    const float u24 = float(uint32_t(w >> 40)) * 0x1.0p-24f;
+    return __fmul_rd(u24, S);
+}
 template <>
-__device__ __forceinline__ double cmp_value<double>(double t) { return t; }
+__device__ __forceinline__ double draw_target<double>(uint64_t w, double S) { return u53(w) * S; }
 
 template <typename T>
 __device__ __forceinline__ const T *tab_mix(const ChainTab &tb);
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     const int wpc = blockDim.x >> 5;
     unsigned char *gsm = smem_raw + size_t(warp * G::GPW + gw) * G::GROUP_BYTES;
     V *xbuf = reinterpret_cast<V *>(gsm);
-    T *mix = reinterpret_cast<T *>(gsm + G::XBUF);
+    V *mix = reinterpret_cast<V *>(gsm + G::XBUF);
     T *g2 = reinterpret_cast<T *>(gsm + G::XBUF + G::MIXB);
     V *wx = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B);
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         __syncwarp(gmask);
         {
             const T *src = tab_mix<T>(tb);
-            for (int j = gl; j < L; j += GW) mix[j] = src[j];
+            for (int j = gl; j < L; j += GW) mix[j] = vsplat(src[j]);
             const T *gs = tab_g<T>(tb);
             for (int j = gl; j < 2 * L; j += GW) g2[j] = gs[j < L ? j : j - L];
         }
@@ -323,8 +329,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             }
             const int wsel = lb & 3;
             const uint64_t myw = wsel == 0 ? wd0 : wsel == 1 ? wd1 : wsel == 2 ? wd2 : wd3;
-            const double u0 = u53(__shfl_sync(gmask, myw, 0, GW));
-            const double u1 = u53(__shfl_sync(gmask, myw, 1, GW));
+            const uint64_t uw0 = __shfl_sync(gmask, myw, 0, GW);
+            const uint64_t uw1 = __shfl_sync(gmask, myw, 1, GW);
 
             // p(y) = max(f, 0) g(ix - cx) g(iy - cy): x-weights shared through wx
             const int cx0 = cur0 % L, cy0 = cur0 / L, cx1 = cur1 % L, cy1 = cur1 / L;
@@ -358,8 +364,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             }
             const T S0 = __shfl_sync(gmask, in0, L - 1, GW);
             const T S1 = __shfl_sync(gmask, in1, L - 1, GW);
-            const T t0 = cmp_value<T>(u0 * double(S0));
-            const T t1 = cmp_value<T>(u1 * double(S1));
+            const T t0 = draw_target<T>(uw0, S0);
+            const T t1 = draw_target<T>(uw1, S1);
             // the row that holds the crossing, then the first column whose prefix crosses:
             // the count of prefixes at or below the lane's remaining threshold
             const T r0 = t0 - ex0, r1 = t1 - ex1;
