@@ -123,6 +123,17 @@ int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
  * reset != 0 zeroes the accumulators after reading.  Errors: HQMC_ERR_STATE, _CUDA. */
 int hqmc_measure(hqmc_ctx *ctx, hqmc_obs *out, double *Sk, double *Cr, int reset);
 
+/* Checkpoint format of hqmc_log_weight_grad's reverse pass.  The forward pass keeps
+ * F_l = W_l . alpha_l only every `stride` slices (0 = ceil(sqrt M)) and the reverse pass
+ * recomputes each stride-long segment from its checkpoint.
+ *   HQMC_CKPT_BF16  (FP32 context) checkpoints as BF16 with the slice's power-of-two
+ *                   exponent; recomputed F carries the BF16 rounding (relative 2^-9)
+ *   HQMC_CKPT_FULL  checkpoints in the context's own precision (exact recompute)
+ * The FP64 context always keeps FP64 checkpoints.  Errors: HQMC_ERR_ARG. */
+#define HQMC_CKPT_BF16 0
+#define HQMC_CKPT_FULL 1
+int hqmc_set_checkpoint(hqmc_ctx *ctx, int stride, int kind);
+
 /* Log-weight of the current worldlines with every worldline anchored at slice 0 on its
  * current site, and its gradient (the adjoint of the forward filter of Eq. ffbsFwd):
  *   logZ[c]      = sum_{sigma,p} log Z_p                                      (host [n_chains])
@@ -131,8 +142,11 @@ int hqmc_measure(hqmc_ctx *ctx, hqmc_obs *out, double *Sk, double *Cr, int reset
  *                  over chains, element type float (FP32 context) or double (FP64)
  *   dlogZ_dt[c]  = d logZ / d t                                              (host [n_chains])
  * v (nullable, device, same type and layout as dlogZ_dv) replaces log W = sigma lambda s.
- * Any output pointer may be NULL.  The FP32 context checkpoints alpha every ceil(sqrt M)
- * slices in BF16 with a per-slice exponent and recomputes in between.
+ * Any output pointer may be NULL; dlogZ_dv is zeroed by the call before accumulation
+ * (FP32 atomics: the summation order over worldlines is not fixed).  The reverse pass
+ * checkpoints as set by hqmc_set_checkpoint (default: every ceil(sqrt M) slices, BF16 with
+ * a per-slice exponent in an FP32 context).  The first call allocates the context's
+ * adjoint scratch with cudaMalloc (freed by hqmc_destroy).  Blocks until done.
  * Errors: HQMC_ERR_STATE, HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
 int hqmc_log_weight_grad(hqmc_ctx *ctx, const void *v, double *logZ, void *dlogZ_dv,
                          double *dlogZ_dt);

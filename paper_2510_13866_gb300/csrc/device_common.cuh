@@ -266,28 +266,73 @@ __device__ __forceinline__ void fft(cvec<V> (&a)[N]) {
     }
 }
 
-// Periodic convolution of one lattice line of both worldlines with the even real line
-// kernel g: v <- g * v.
-//
-// Even L: the line is packed as n = L/2 complex values z_m = v_{2m} + i v_{2m+1}.  With
-// Z = DFT_n(z), the half-spectrum identities of a real DFT give the packed transform of
-// the convolved line directly as
-//     Z'_k = alpha_k Z_k + i beta_k conj(Z_{(n-k) mod n})
-// with theta_k = 2 pi k / L, P_k = (gh_k + gh_{k+n}) / 2, Q_k = (gh_k - gh_{k+n}) / 2,
-//     alpha_k = (P_k - Q_k sin theta_k) / n,   beta_k = Q_k cos theta_k / n,
-// gh the L-point DFT of g; then z' = IDFT_n(Z') unpacks to the convolved line.  Two
-// half-size complex FFTs per line, all arithmetic on two-worldline vectors.
-// Odd L: full-size complex DFT of the real line, multiply by gh_k / L, inverse DFT.
-// `mix` holds alpha_k, beta_k interleaved (even L) or gh_k / L (odd L), each already
-// broadcast to both components.
+// Building blocks of conv_line with the spectrum exposed, for passes that apply more
+// than one line kernel to the same line (the adjoint applies g and dg/dt):
+//   line_fwd: spectrum of the line (even L: DFT_n of the packed line, odd L: DFT_L)
+//   spec_mix: out = mix(in), or out += mix(in) with ACC (out must not alias in)
+//   line_inv: the line whose spectrum is z (the 1/n or 1/L factor is in the mix)
+template <int L>
+struct line_spec {
+    static constexpr int K = (L % 2 == 0) ? L / 2 : L;
+};
+
 template <int L, typename V>
-__device__ __forceinline__ void conv_line(V (&v)[L], const V *mix) {
+__device__ __forceinline__ void line_fwd(const V (&v)[L], cvec<V> (&z)[line_spec<L>::K]) {
+    if constexpr (L % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < L / 2; ++m) z[m] = {v[2 * m], v[2 * m + 1]};
+    } else {
+#pragma unroll
+        for (int m = 0; m < L; ++m) z[m] = {v[m], vzero(v[m])};
+    }
+    fft<line_spec<L>::K, -1>(z);
+}
+
+template <int L, typename V>
+__device__ __forceinline__ void line_inv(cvec<V> (&z)[line_spec<L>::K], V (&v)[L]) {
+    fft<line_spec<L>::K, +1>(z);
+    if constexpr (L % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < L / 2; ++m) {
+            v[2 * m] = z[m].re;
+            v[2 * m + 1] = z[m].im;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < L; ++m) v[m] = z[m].re;
+    }
+}
+
+template <int L, bool ACC, typename V>
+__device__ __forceinline__ void spec_mix(cvec<V> (&out)[line_spec<L>::K], const cvec<V> (&in)[line_spec<L>::K],
+                                         const V *mix) {
     if constexpr (L % 2 == 0) {
         constexpr int n = L / 2;
-        cvec<V> z[n];
+        static_for<0, n>([&](auto KI) {
+            constexpr int k = decltype(KI)::value;
+            constexpr int kp = (n - k) % n;
+            V al, be;
+            load_mix(mix, k, al, be);
+            const V re = vfma(in[k].re, al, vmul(in[kp].im, be));
+            const V im = vfma(in[k].im, al, vmul(in[kp].re, be));
+            if constexpr (ACC) out[k] = {vadd(out[k].re, re), vadd(out[k].im, im)};
+            else out[k] = {re, im};
+        });
+    } else {
 #pragma unroll
-        for (int m = 0; m < n; ++m) z[m] = {v[2 * m], v[2 * m + 1]};
-        fft<n, -1>(z);
+        for (int k = 0; k < L; ++k) {
+            const V w = load_mix1(mix, k);
+            if constexpr (ACC) out[k] = {vfma(in[k].re, w, out[k].re), vfma(in[k].im, w, out[k].im)};
+            else out[k] = {vmul(in[k].re, w), vmul(in[k].im, w)};
+        }
+    }
+}
+
+// in-place spectral mix (even L: the pairs (k, n-k) are read before either is written)
+template <int L, typename V>
+__device__ __forceinline__ void spec_mix_inplace(cvec<V> (&z)[line_spec<L>::K], const V *mix) {
+    if constexpr (L % 2 == 0) {
+        constexpr int n = L / 2;
         static_for<0, n>([&](auto KI) {
             constexpr int k = decltype(KI)::value;
             constexpr int kp = (n - k) % n;
@@ -305,26 +350,35 @@ __device__ __forceinline__ void conv_line(V (&v)[L], const V *mix) {
                 z[kp] = {vfma(zp.re, a1, vmul(zk.im, b1)), vfma(zp.im, a1, vmul(zk.re, b1))};
             }
         });
-        fft<n, +1>(z);
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-            v[2 * m] = z[m].re;
-            v[2 * m + 1] = z[m].im;
-        }
     } else {
-        cvec<V> z[L];
-#pragma unroll
-        for (int m = 0; m < L; ++m) z[m] = {v[m], vzero(v[m])};
-        fft<L, -1>(z);
 #pragma unroll
         for (int k = 0; k < L; ++k) {
             const V w = load_mix1(mix, k);
             z[k] = {vmul(z[k].re, w), vmul(z[k].im, w)};
         }
-        fft<L, +1>(z);
-#pragma unroll
-        for (int m = 0; m < L; ++m) v[m] = z[m].re;
     }
+}
+
+// Periodic convolution of one lattice line of both worldlines with the even real line
+// kernel g: v <- g * v.
+//
+// Even L: the line is packed as n = L/2 complex values z_m = v_{2m} + i v_{2m+1}.  With
+// Z = DFT_n(z), the half-spectrum identities of a real DFT give the packed transform of
+// the convolved line directly as
+//     Z'_k = alpha_k Z_k + i beta_k conj(Z_{(n-k) mod n})
+// with theta_k = 2 pi k / L, P_k = (gh_k + gh_{k+n}) / 2, Q_k = (gh_k - gh_{k+n}) / 2,
+//     alpha_k = (P_k - Q_k sin theta_k) / n,   beta_k = Q_k cos theta_k / n,
+// gh the L-point DFT of g; then z' = IDFT_n(Z') unpacks to the convolved line.  Two
+// half-size complex FFTs per line, all arithmetic on two-worldline vectors.
+// Odd L: full-size complex DFT of the real line, multiply by gh_k / L, inverse DFT.
+// `mix` holds alpha_k, beta_k interleaved (even L) or gh_k / L (odd L), each already
+// broadcast to both components.
+template <int L, typename V>
+__device__ __forceinline__ void conv_line(V (&v)[L], const V *mix) {
+    cvec<V> z[line_spec<L>::K];
+    line_fwd<L>(v, z);
+    spec_mix_inplace<L>(z, mix);
+    line_inv<L>(z, v);
 }
 
 // ---------------------------------------------------------------------------------

@@ -25,6 +25,8 @@ struct ChainTab {
     // interleaved for k = 0..L/2-1; odd L: ghat(k) for k = 0..L-1
     double mix_d[kMaxL];
     float mix_f[kMaxL];
+    double mixd_d[kMaxL];  // the same for the kernel d g / dt (adjoint)
+    float mixd_f[kMaxL];
     double pplus[2 * kPTab + 1];  // 1 / (1 + e^{-2 lambda m}), m = -kPTab..kPTab
 };
 
@@ -82,6 +84,25 @@ struct FfbsLaunch {
     int M_max;                 // largest M in the class (scratch slot size)
     void *scratch;             // slots of M_max * L * L complex values
     long long slot_elems;      // complex elements per slot
+};
+
+// One launch of the adjoint kernel covers the chains of one lattice size.
+struct GradLaunch {
+    const int *class_chains;
+    const int *class_pair_off;
+    int nclass;
+    int total_pairs;
+    int K;                     // checkpoint stride (slices)
+    int ckpt_bf16;             // 1: checkpoints as BF16 pairs, 0: in the context precision
+    void *ckpt;                // per group: [nseg][N] checkpoint elements, then [nseg][2] int exponents
+    long long ckpt_bytes;      // bytes per group
+    long long ckpt_exp_off;    // byte offset of the exponents within a group's block
+    void *seg;                 // per group: [K][N] recomputed F_l (context precision pairs)
+    long long seg_elems;       // pair elements per group
+    const void *v;             // optional log-potential, [2][M][N] per chain (nullable)
+    void *dv;                  // d log Z / d v, same layout (nullable), zeroed by the caller
+    double *logz;              // [chain], zeroed by the caller
+    double *dt;                // [chain], zeroed by the caller
 };
 
 // Launchers (defined in the per-precision translation units).

@@ -17,12 +17,11 @@ cudaError_t ffbs_occupancy_f32(int L, int wpc, int *blocks);
 cudaError_t ffbs_occupancy_f64(int L, int wpc, int *blocks);
 size_t ffbs_smem_f32(int L, int wpc);
 size_t ffbs_smem_f64(int L, int wpc);
-cudaError_t launch_grad(const DevState &st, bool fp64, int L, const int *class_chains, const int *class_wl_off,
-                        int nclass, int total_pairs, const void *v, void *dv, double *logz_wl, double *dt_wl,
-                        void *ckpt, long long ckpt_elems, int K, int grid, cudaStream_t s);
-size_t grad_ckpt_bytes_per_group(bool fp64, int L, int M);
-int grad_groups_per_cta(int L);
-bool grad_supported(int L);
+cudaError_t launch_grad_f32(int L, const DevState &st, const GradLaunch &gk, int grid, cudaStream_t s);
+cudaError_t launch_grad_f64(int L, const DevState &st, const GradLaunch &gk, int grid, cudaStream_t s);
+cudaError_t grad_occupancy_f32(int L, int *blocks);
+cudaError_t grad_occupancy_f64(int L, int *blocks);
+constexpr int kGradWarpsHost = 4;  // warps per CTA of the adjoint kernel (fixed)
 
 static const int kSizes[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
 
@@ -95,8 +94,12 @@ struct hqmc_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
-    // gradient resources
-    std::vector<int> grad_cls_off;
+    // adjoint: checkpoint stride (0 = ceil(sqrt M)) and format, context-owned scratch
+    int ckpt_stride = 0;
+    int ckpt_kind = HQMC_CKPT_BF16;
+    unsigned char *grad_mem = nullptr;
+    size_t grad_bytes = 0;
+    long long total_v = 0;
 
     // per-phase timing: events [4 * slot]: ffbs start, ffbs end, slice start, slice end
     int prof_max = 0, prof_n = 0;
@@ -157,19 +160,30 @@ void build_tab(const HostChain &h, ChainTab &tb, double lam) {
     }
     // spectral mix of conv_line: with n = L/2, P = (gh_k + gh_{k+n})/2, Q = (gh_k - gh_{k+n})/2,
     // alpha_k = (P - Q sin(2 pi k/L)) / n and beta_k = Q cos(2 pi k/L) / n (gh unnormalised)
+    // (mixd: the same for d gh / dt = 2 dtau cos(2 pi k/L) gh_k)
+    auto ghk = [&](double th) { return std::exp(2.0 * z * std::cos(th)); };
+    auto dghk = [&](double th) { return 2.0 * h.dtau * std::cos(th) * std::exp(2.0 * z * std::cos(th)); };
     if (L % 2 == 0) {
         const int n = L / 2;
         for (int k = 0; k < n; ++k) {
-            const double th = two_pi * k / L;
-            const double ga = std::exp(2.0 * z * std::cos(th)), gb = std::exp(2.0 * z * std::cos(th + 0.5 * two_pi));
-            const double P = 0.5 * (ga + gb), Q = 0.5 * (ga - gb);
+            const double th = two_pi * k / L, th2 = th + 0.5 * two_pi;
+            const double P = 0.5 * (ghk(th) + ghk(th2)), Q = 0.5 * (ghk(th) - ghk(th2));
             tb.mix_d[2 * k] = (P - Q * std::sin(th)) / n;
             tb.mix_d[2 * k + 1] = Q * std::cos(th) / n;
+            const double Pd = 0.5 * (dghk(th) + dghk(th2)), Qd = 0.5 * (dghk(th) - dghk(th2));
+            tb.mixd_d[2 * k] = (Pd - Qd * std::sin(th)) / n;
+            tb.mixd_d[2 * k + 1] = Qd * std::cos(th) / n;
         }
     } else {
-        for (int k = 0; k < L; ++k) tb.mix_d[k] = std::exp(2.0 * z * std::cos(two_pi * k / L)) / L;
+        for (int k = 0; k < L; ++k) {
+            tb.mix_d[k] = ghk(two_pi * k / L) / L;
+            tb.mixd_d[k] = dghk(two_pi * k / L) / L;
+        }
     }
-    for (int k = 0; k < L; ++k) tb.mix_f[k] = float(tb.mix_d[k]);
+    for (int k = 0; k < L; ++k) {
+        tb.mix_f[k] = float(tb.mix_d[k]);
+        tb.mixd_f[k] = float(tb.mixd_d[k]);
+    }
     std::vector<double> g;
     ring_propagator(L, z, g);
     for (int d = 0; d < L; ++d) {
@@ -311,6 +325,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     }
     c->total_N = size_t(mb);
     c->total_wl = lb;
+    c->total_v = vb;
     const size_t o_s = take(size_t(sb) * 4);
     const size_t o_x = take(size_t(xb) * 2);
     const size_t o_h = take(size_t(hb) * 4);
@@ -872,13 +887,98 @@ int hqmc_set_state(hqmc_ctx *c, int chain, const int8_t *s, const int32_t *x, co
     return HQMC_OK;
 }
 
-int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_dv, double *dlogZ_dt) {
-    (void)v;
-    (void)logZ;
-    (void)dlogZ_dv;
-    (void)dlogZ_dt;
+int hqmc_set_checkpoint(hqmc_ctx *c, int stride, int kind) {
     if (!c) return HQMC_ERR_ARG;
-    return fail(c, HQMC_ERR_UNSUPPORTED, "log_weight_grad is not built yet");
+    if (stride < 0) return fail(c, HQMC_ERR_ARG, "checkpoint stride must be >= 0");
+    if (kind != HQMC_CKPT_BF16 && kind != HQMC_CKPT_FULL) return fail(c, HQMC_ERR_ARG, "unknown checkpoint kind");
+    c->ckpt_stride = stride;
+    c->ckpt_kind = kind;
+    return HQMC_OK;
+}
+
+int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_dv, double *dlogZ_dt) {
+    if (!c) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    const bool f64 = c->precision == HQMC_FP64;
+    const bool bf16 = !f64 && c->ckpt_kind == HQMC_CKPT_BF16;
+    const size_t vsz = f64 ? 16 : 8;             // one element of a worldline pair
+    const size_t tsz = f64 ? 8 : 4;              // one element of v / dv
+    struct Plan {
+        int K, nseg, grid;
+        long long groups;
+        size_t ck_bytes, ck_exp_off, seg_elems, off;
+    };
+    std::vector<Plan> plans(c->classes.size());
+    size_t off = round_up(size_t(c->nchains) * 16, 256);  // logz, dt per chain
+    for (size_t k = 0; k < c->classes.size(); ++k) {
+        const LClass &cl = c->classes[k];
+        Plan &p = plans[k];
+        const int M = cl.M_max;
+        p.K = c->ckpt_stride > 0 ? std::min(c->ckpt_stride, M) : std::max(1, int(std::ceil(std::sqrt(double(M)))));
+        p.nseg = (M + p.K - 1) / p.K;
+        const size_t N = size_t(cl.L) * cl.L;
+        p.ck_exp_off = round_up(size_t(p.nseg) * N * (bf16 ? 4 : vsz), 16);
+        p.ck_bytes = round_up(p.ck_exp_off + size_t(p.nseg) * 8, 256);
+        p.seg_elems = size_t(p.K) * N;
+        int bps = 1;
+        cudaError_t e = f64 ? grad_occupancy_f64(cl.L, &bps) : grad_occupancy_f32(cl.L, &bps);
+        if (e != cudaSuccess) return cuda_fail(c, e, "grad occupancy");
+        bps = std::max(1, bps);
+        const int gpc = kGradWarpsHost * ffbs_groups_per_warp(cl.L);
+        const int need = (cl.total_pairs + gpc - 1) / gpc;
+        p.grid = std::max(1, std::min(need, bps * c->num_sms));
+        p.groups = (long long)p.grid * gpc;
+        p.off = off;
+        off = round_up(off + size_t(p.groups) * (p.ck_bytes + p.seg_elems * vsz), 256);
+    }
+    if (off > c->grad_bytes) {
+        if (c->grad_mem) cudaFree(c->grad_mem);
+        c->grad_mem = nullptr;
+        c->grad_bytes = 0;
+        void *m = nullptr;
+        cudaError_t e = cudaMalloc(&m, off);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, HQMC_ERR_NOMEM, std::string("cudaMalloc (adjoint scratch): ") + cudaGetErrorString(e));
+        }
+        c->grad_mem = static_cast<unsigned char *>(m);
+        c->grad_bytes = off;
+    }
+    cudaStream_t st = c->stream;
+    double *d_logz = reinterpret_cast<double *>(c->grad_mem);
+    double *d_dt = d_logz + c->nchains;
+    HQMC_CUDA(c, cudaMemsetAsync(d_logz, 0, size_t(c->nchains) * 16, st));
+    if (dlogZ_dv) HQMC_CUDA(c, cudaMemsetAsync(dlogZ_dv, 0, size_t(c->total_v) * tsz, st));
+    for (size_t k = 0; k < c->classes.size(); ++k) {
+        const LClass &cl = c->classes[k];
+        const Plan &p = plans[k];
+        GradLaunch gk{};
+        gk.class_chains = reinterpret_cast<const int *>(c->base + cl.cls_off);
+        gk.class_pair_off = gk.class_chains + cl.chains.size();
+        gk.nclass = int(cl.chains.size());
+        gk.total_pairs = cl.total_pairs;
+        gk.K = p.K;
+        gk.ckpt_bf16 = bf16 ? 1 : 0;
+        gk.ckpt = c->grad_mem + p.off;
+        gk.ckpt_bytes = (long long)p.ck_bytes;
+        gk.ckpt_exp_off = (long long)p.ck_exp_off;
+        gk.seg = c->grad_mem + p.off + size_t(p.groups) * p.ck_bytes;
+        gk.seg_elems = (long long)p.seg_elems;
+        gk.v = v;
+        gk.dv = dlogZ_dv;
+        gk.logz = d_logz;
+        gk.dt = d_dt;
+        cudaError_t e = f64 ? launch_grad_f64(cl.L, c->st, gk, p.grid, st) : launch_grad_f32(cl.L, c->st, gk, p.grid, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "grad launch");
+    }
+    std::vector<double> h(2 * size_t(c->nchains));
+    HQMC_CUDA(c, cudaMemcpyAsync(h.data(), d_logz, h.size() * 8, cudaMemcpyDeviceToHost, st));
+    HQMC_CUDA(c, cudaStreamSynchronize(st));
+    if (logZ) std::memcpy(logZ, h.data(), size_t(c->nchains) * 8);
+    if (dlogZ_dt) std::memcpy(dlogZ_dt, h.data() + c->nchains, size_t(c->nchains) * 8);
+    return check_status(c);
 }
 
 int hqmc_set_profiling(hqmc_ctx *c, int max_sweeps) {
@@ -920,6 +1020,7 @@ void hqmc_destroy(hqmc_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_layout(c);
+    if (c->grad_mem) cudaFree(c->grad_mem);
     for (auto s : c->aux) cudaStreamDestroy(s);
     for (auto e : c->ev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

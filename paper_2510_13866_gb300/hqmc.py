@@ -13,6 +13,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhqmc.so")
 
 HQMC_FP32, HQMC_FP64 = 0, 1
+HQMC_CKPT_BF16, HQMC_CKPT_FULL = 0, 1
 ERRORS = {
     -1: "HQMC_ERR_ARG", -2: "HQMC_ERR_NOMEM", -3: "HQMC_ERR_CUDA", -4: "HQMC_ERR_TIMEOUT",
     -5: "HQMC_ERR_STATE", -6: "HQMC_ERR_UNSUPPORTED", -7: "HQMC_ERR_NUMERIC", -8: "HQMC_ERR_SCRATCH",
@@ -29,6 +30,7 @@ SIGNATURES = {
     "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
     "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "hqmc_set_checkpoint": (_i, [_vp, _i, _i]),
     "hqmc_log_weight_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "hqmc_chain_shape": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hqmc_get_state": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
@@ -106,6 +108,7 @@ class Lattice:
         stream = torch.cuda.current_stream(device)
         self._check(lib().hqmc_set_stream(self._ctx, C.c_void_p(stream.cuda_stream)))
         self.shapes = None
+        self.params = None
 
     # -- helpers -----------------------------------------------------------
     def _check(self, rc, ctx=True):
@@ -128,7 +131,14 @@ class Lattice:
     # -- configuration -----------------------------------------------------
     def set_params(self, t, U, beta, dtau, filling, chain=-1):
         self._check(lib().hqmc_set_params(self._ctx, chain, t, U, beta, dtau, filling))
+        if chain == -1:
+            self.params = (float(t), float(U), float(beta), float(dtau), float(filling))
         self.shapes = None
+
+    def set_checkpoint(self, stride=0, bf16=True):
+        """Checkpoint stride of the adjoint's reverse pass (0 = ceil(sqrt M)) and format
+        (BF16 with a per-slice exponent, or the context's own precision)."""
+        self._check(lib().hqmc_set_checkpoint(self._ctx, int(stride), HQMC_CKPT_BF16 if bf16 else HQMC_CKPT_FULL))
 
     def set_launch(self, use_graph=True, persistent=True, warps_per_cta=0):
         self._check(lib().hqmc_set_launch(self._ctx, int(use_graph), int(persistent), int(warps_per_cta)))
@@ -243,3 +253,53 @@ class Lattice:
         self._check(lib().hqmc_log_weight_grad(self._ctx, vp, _ptr(lz),
                                                None if dv is None else C.c_void_p(dv.data_ptr()), _ptr(ddt)))
         return lz, dv, ddt
+
+
+def _log_weight_function():
+    import torch
+
+    class LogWeight(torch.autograd.Function):
+        """log Z of every chain (worldlines anchored at slice 0 on their current sites) as a
+        function of the log-potential v (packed [2][M][N] per chain) and the hopping t.
+
+        The forward and the adjoint both run in libhqmc.so (one hqmc_log_weight_grad
+        call); backward only scales the saved per-chain gradients by the incoming ones."""
+
+        @staticmethod
+        def forward(ctx, lat, v, t):
+            tv = float(t)
+            if lat.params is None:
+                raise ValueError("set_params first")
+            if tv != lat.params[0]:
+                lat.set_params(tv, *lat.params[1:])
+            lz, dv, dt = lat.log_weight_grad(v=v.detach(), want_dv=True)
+            sizes = [2 * M * L * L for L, M, _ in lat.shapes]
+            ctx.save_for_backward(dv)
+            ctx.sizes = sizes
+            ctx.dt = torch.as_tensor(dt, dtype=torch.float64)
+            ctx.t_shape = t.shape if torch.is_tensor(t) else None
+            return torch.as_tensor(lz, dtype=torch.float64, device=v.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (dv,) = ctx.saved_tensors
+            rep = torch.repeat_interleave(g.to(dv.dtype), torch.as_tensor(ctx.sizes, device=g.device))
+            gv = dv * rep
+            gt = None
+            if ctx.t_shape is not None:
+                gt = (g.detach().cpu() * ctx.dt).sum().to(torch.float64).reshape(ctx.t_shape)
+            return None, gv, gt
+
+    return LogWeight
+
+
+_LW = None
+
+
+def log_weight(lat, v, t):
+    """Differentiable log Z per chain: torch.autograd sees v (device tensor of the context's
+    dtype, packed [2][M][N] per chain) and t (a 0-d CPU tensor)."""
+    global _LW
+    if _LW is None:
+        _LW = _log_weight_function()
+    return _LW.apply(lat, v, t)

@@ -1,0 +1,173 @@
+"""GPU adjoint (hqmc_log_weight_grad) against the FP64 oracle's forward-backward pass.
+
+Every worldline is anchored at slice 0 on its current site.  Compared per chain:
+  log Z          sum over worldlines of the filter log-weight
+  dlogZ/dv       summed forward-backward site marginals, [2][M][N]
+  dlogZ/dt       d log Z / d t
+Tolerances: with checkpoints in the context precision the reverse pass recomputes F_l
+exactly, so the FP32 bounds are those of FP32 FFT messages (log Z 1e-5 relative, the
+rest 1e-4 relative to their scale); FP64 is held to 1e-10.  BF16 checkpoints round each
+checkpointed F_l to 8 significant bits (relative 2^-9), so marginals and dlogZ/dt are
+held to 2^-6 of their scale, log Z (forward pass, no checkpoint) stays at 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def make(L, seeds, prec, params, sweeps=2):
+    from paper_2510_13866_gb300 import Lattice
+
+    lat = Lattice(L, seeds, precision=prec)
+    lat.set_params(*params)
+    if sweeps:
+        lat.sweep(sweeps)
+    return lat
+
+
+def oracle_grad(lat, c, params, v=None):
+    L = int(lat.Ls[c])
+    orc = oracle.Chain(L, *params, int(lat.seeds[c]))
+    s, x, _, _ = lat.get_state(c)
+    orc.s[:] = s
+    orc.x[:] = x
+    return orc.grad(v)
+
+
+def split(lat, dv):
+    out, o = [], 0
+    for L, M, _ in lat.shapes:
+        n = 2 * M * L * L
+        out.append(dv[o:o + n].reshape(2, M, L * L))
+        o += n
+    return out
+
+
+def check(lat, params, tol_lz, tol_g, chains, v=None, v_np=None):
+    lz, dv, dt = lat.log_weight_grad(v=v)
+    dvs = split(lat, dv.double().cpu().numpy())
+    for c in chains:
+        rz, rdv, rdt = oracle_grad(lat, c, params, None if v_np is None else v_np[c])
+        assert abs(lz[c] - rz) <= tol_lz * max(1.0, abs(rz)), (c, lz[c], rz)
+        scale = max(1.0, np.abs(rdv).max())
+        assert np.abs(dvs[c] - rdv).max() <= tol_g * scale, (c, np.abs(dvs[c] - rdv).max())
+        assert abs(dt[c] - rdt) <= tol_g * max(1.0, abs(rdt)), (c, dt[c], rdt)
+    return lz, dvs, dt
+
+
+@pytest.mark.parametrize("prec,L,beta,dtau,fill,stride", [
+    ("fp32", 4, 1.0, 0.1, 1.0, 0),
+    ("fp32", 8, 0.8, 0.1, 0.5, 3),
+    ("fp32", 16, 1.0, 0.05, 1.0, 0),
+    ("fp32", 3, 0.6, 0.1, 2 / 9 * 2, 1),
+    ("fp32", 12, 0.5, 0.05, 0.875, 4),
+    ("fp64", 8, 0.8, 0.1, 1.0, 0),
+    ("fp64", 6, 0.5, 0.1, 1 / 3, 2),
+])
+def test_grad_full_checkpoints_match_oracle(prec, L, beta, dtau, fill, stride):
+    params = (1.0, 4.0, beta, dtau, fill)
+    lat = make(L, [3, 11], prec, params)
+    lat.set_checkpoint(stride, bf16=False)
+    tol = (1e-5, 1e-4) if prec == "fp32" else (1e-10, 1e-10)
+    check(lat, params, *tol, chains=[0, 1])
+    lat.close()
+
+
+def test_grad_bf16_checkpoints_within_bf16_bound():
+    params = (1.0, 4.0, 1.0, 0.05, 1.0)
+    lat = make(16, [5], "fp32", params)
+    lat.set_checkpoint(0, bf16=True)  # every ceil(sqrt 20) = 5 slices
+    lz, dvs, dt = check(lat, params, 1e-5, 2.0 ** -6, chains=[0])
+    lat.close()
+
+
+def test_grad_with_given_log_potential():
+    import torch
+
+    params = (1.0, 2.0, 0.6, 0.1, 0.5)
+    L = 6
+    lat = make(L, [7, 8], "fp64", params, sweeps=1)
+    _, M, _ = lat.shapes[0]
+    rng = np.random.default_rng(3)
+    v_np = [rng.normal(0.0, 0.5, size=(2, M, L * L)) for _ in range(2)]
+    v = torch.from_numpy(np.concatenate([a.ravel() for a in v_np])).cuda()
+    check(lat, params, 1e-10, 1e-10, chains=[0, 1], v=v, v_np=v_np)
+    lat.close()
+
+
+def test_grad_marginals_sum_to_worldline_counts():
+    params = (1.0, 4.0, 1.0, 0.05, 1.0)
+    lat = make(8, [1, 2, 3], "fp32", params)
+    dv = split(lat, lat.log_weight_grad()[1].double().cpu().numpy())
+    for c in range(3):
+        _, M, Ns = lat.shapes[c]
+        assert np.allclose(dv[c].sum(axis=2), Ns, rtol=1e-5)
+        # slice 0 holds the anchors: its marginal is the anchor occupancy
+        _, x, _, _ = lat.get_state(c)
+        for sg in range(2):
+            occ = np.bincount(x[sg, :, 0], minlength=64)
+            assert np.allclose(dv[c][sg, 0], occ, atol=1e-4)
+    lat.close()
+
+
+def test_dt_against_gpu_finite_differences():
+    """FP64 context: d log Z / dt against central differences of its own log Z (h = 1e-6)."""
+    params = [1.0, 4.0, 0.8, 0.1, 1.0]
+    lat = make(8, [4], "fp64", params)
+    lz, _, dt = lat.log_weight_grad()
+    h = 1e-6
+    lat.set_params(1.0 + h, *params[1:])
+    zp = lat.log_weight_grad()[0][0]
+    lat.set_params(1.0 - h, *params[1:])
+    zm = lat.log_weight_grad()[0][0]
+    fd = (zp - zm) / (2 * h)
+    assert abs(fd - dt[0]) <= 1e-6 * max(1.0, abs(dt[0])), (fd, dt[0])
+    lat.close()
+
+
+def test_autograd_function_matches_adjoint():
+    import torch
+
+    from paper_2510_13866_gb300 import log_weight
+
+    params = (1.0, 4.0, 0.5, 0.1, 1.0)
+    lat = make(6, [1, 2], "fp64", params, sweeps=1)
+    lz0, dv0, dt0 = lat.log_weight_grad()
+    # v = sigma lambda s reproduces the default potential
+    lam = oracle.lam(4.0, 0.1)
+    vs = []
+    for c in range(2):
+        s, _, _, _ = lat.get_state(c)
+        vs.append(np.stack([lam * s, -lam * s]).astype(np.float64).ravel())
+    v = torch.from_numpy(np.concatenate(vs)).cuda().requires_grad_(True)
+    t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    lz = log_weight(lat, v, t)
+    assert np.allclose(lz.detach().cpu().numpy(), lz0, rtol=1e-12)
+    w = torch.tensor([0.3, -1.7], dtype=torch.float64, device="cuda")
+    (lz * w).sum().backward()
+    M = lat.shapes[0][1]
+    n = 2 * M * 36
+    ref = torch.cat([dv0[:n] * 0.3, dv0[n:] * -1.7])
+    assert torch.allclose(v.grad, ref, rtol=1e-12, atol=1e-14)
+    assert abs(t.grad.item() - (0.3 * dt0[0] - 1.7 * dt0[1])) < 1e-10 * max(1, abs(t.grad.item()))
+    lat.close()
+
+
+def test_grad_config4_sampled():
+    """L=16 (N=256), U=4, beta=4, dtau=0.05 (M=80), half filling, 128 chains, default BF16
+    checkpoints every 9 slices; oracle check of one chain, invariants on all."""
+    params = (1.0, 4.0, 4.0, 0.05, 1.0)
+    lat = make(16, list(range(128)), "fp32", params, sweeps=1)
+    lz, dv, dt = lat.log_weight_grad()
+    dvs = split(lat, dv.double().cpu().numpy())
+    assert np.all(np.isfinite(lz)) and np.all(np.isfinite(dt))
+    for c in range(128):
+        assert np.allclose(dvs[c].sum(axis=2), 128, rtol=1e-4)
+    rz, rdv, rdt = oracle_grad(lat, 77, params)
+    assert abs(lz[77] - rz) <= 1e-5 * abs(rz)
+    assert np.abs(dvs[77] - rdv).max() <= 2.0 ** -6 * np.abs(rdv).max()
+    assert abs(dt[77] - rdt) <= 2.0 ** -6 * abs(rdt)
+    lat.close()
