@@ -181,10 +181,11 @@ def main():
         return float(t.item())
 
     from paper_2510_13866_gb300 import Lattice
+    from paper_2510_13866_gb300.shard import chain_seeds
 
     w = dict(WORK)
     w["chains"] = args.chains
-    seeds = [rank * w["chains"] + c for c in range(w["chains"])]
+    seeds = chain_seeds(rank, w["chains"])
     lat = Lattice(w["L"], seeds, precision="fp32", device=local)
     lat.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
     lat.prepare()
