@@ -69,7 +69,9 @@ typedef struct {
 
 /* Create a context for n_chains independent chains on CUDA device `device`.
  *   L[c]      linear size of chain c's lattice; 2 <= L[c] and L[c] must be one of the
- *             sizes built into the library (hqmc_supported_L), else HQMC_ERR_UNSUPPORTED.
+ *             sizes built into the library (hqmc_supported_L), else HQMC_ERR_UNSUPPORTED:
+ *             2, 3, 4, 6, 8, 12, 16, 24, 32 in both precisions; 48, 64, 128 in FP32 only
+ *             (one CTA per worldline pair; hqmc_log_weight_grad covers L <= 32).
  *   seeds[c]  Philox key of chain c.
  *   precision HQMC_FP32 or HQMC_FP64.
  * *out receives the context (caller frees it with hqmc_destroy).  No device memory is

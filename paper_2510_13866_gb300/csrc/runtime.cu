@@ -23,13 +23,20 @@ cudaError_t grad_occupancy_f32(int L, int *blocks);
 cudaError_t grad_occupancy_f64(int L, int *blocks);
 constexpr int kGradWarpsHost = 4;  // warps per CTA of the adjoint kernel (fixed)
 
-static const int kSizes[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+cudaError_t launch_ffbs_big(int L, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s);
+cudaError_t ffbs_big_occupancy(int L, int *blocks);
+bool ffbs_big_supported(int L);
+
+// register-line sizes (one warp-group per pair, FP32 and FP64) and wide sizes (one CTA
+// per pair, FP32 only)
+static const int kSizes[] = {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128};
 
 bool ffbs_supported(int L) {
     for (int s : kSizes)
-        if (s == L) return true;
+        if (s == L && s <= 32) return true;
     return false;
 }
+static bool is_big(int L) { return L > 32; }
 int ffbs_groups_per_warp(int L) { return L <= 4 ? 8 : L <= 8 ? 4 : L <= 16 ? 2 : 1; }
 }  // namespace hqmc
 
@@ -254,7 +261,9 @@ void free_layout(hqmc_ctx *c) {
 }
 
 int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
-    cudaError_t e = c->precision == HQMC_FP64 ? ffbs_occupancy_f64(L, wpc, blocks) : ffbs_occupancy_f32(L, wpc, blocks);
+    cudaError_t e = is_big(L) ? ffbs_big_occupancy(L, blocks)
+                    : c->precision == HQMC_FP64 ? ffbs_occupancy_f64(L, wpc, blocks)
+                                                : ffbs_occupancy_f32(L, wpc, blocks);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (*blocks < 1) *blocks = 1;
     return HQMC_OK;
@@ -354,7 +363,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     for (auto &k : c->classes) total_work += double(k.total_pairs) * k.M_max * k.L * k.L * std::log2(double(k.L) + 1);
     for (auto &k : c->classes) {
         const int wpc = default_wpc(c, k.L);
-        const int gpc = wpc * ffbs_groups_per_warp(k.L);
+        const int gpc = is_big(k.L) ? 1 : wpc * ffbs_groups_per_warp(k.L);  // wide lattices: one pair per CTA
         const int need = (k.total_pairs + gpc - 1) / gpc;
         int grid = need;
         if (c->persistent) {
@@ -492,8 +501,9 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.slot_elems = (long long)cl.M_max * cl.L * cl.L;
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
         const int wpc = default_wpc(c, cl.L);
-        cudaError_t e = f64 ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
-                            : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s);
+        cudaError_t e = is_big(cl.L) ? launch_ffbs_big(cl.L, c->st, fl, cl.grid, s)
+                        : f64        ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
+                                     : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "ffbs launch");
     }
     if (nk > 1) {
@@ -567,7 +577,8 @@ int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t
     *out = nullptr;
     for (int i = 0; i < n_chains; ++i) {
         if (L[i] < 2) return HQMC_ERR_ARG;
-        if (!ffbs_supported(L[i])) return HQMC_ERR_UNSUPPORTED;
+        const bool ok = ffbs_supported(L[i]) || (precision == HQMC_FP32 && ffbs_big_supported(L[i]));
+        if (!ok) return HQMC_ERR_UNSUPPORTED;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
@@ -910,6 +921,8 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
         long long groups;
         size_t ck_bytes, ck_exp_off, seg_elems, off;
     };
+    for (const LClass &cl : c->classes)
+        if (is_big(cl.L)) return fail(c, HQMC_ERR_UNSUPPORTED, "the adjoint covers L <= 32");
     std::vector<Plan> plans(c->classes.size());
     size_t off = round_up(size_t(c->nchains) * 16, 256);  // logz, dt per chain
     for (size_t k = 0; k < c->classes.size(); ++k) {

@@ -1,0 +1,102 @@
+"""GPU parity of the wide-lattice FFBS kernel (L = 48, 64, 128; one CTA per worldline
+pair, FP32) against the FP64 oracle, through the C ABI.
+
+The oracle's O(N^2) convolution makes full sweeps at these sizes slow, so each case
+resamples the first few worldlines of each spin in the oracle and compares those:
+log-weights within 1e-5 (relative to max(1, |log Z|)) and paths identical except at a
+first draw within 1e-5 of a CDF edge.  Odd and even M are both covered (the final
+layout of the filter depends on the parity of M).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import path_mismatches, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def run_case(Ls, pars, seeds, nwl):
+    from paper_2510_13866_gb300 import Lattice
+
+    lat = Lattice(Ls, seeds, precision="fp32")
+    for c, p in enumerate(pars):
+        lat.set_params(*p, chain=c)
+    logw = lat.sweep(1, logw=True)
+    stats = []
+    for c, p in enumerate(pars):
+        orc = oracle.Chain(Ls[c], *p, seeds[c])
+        k = nwl[c]
+        ref = orc.sweep(want_margin=True, nwl_limit=k)
+        s, x, a, _ = lat.get_state(c)
+        assert a == ref["anchor"]
+        n = orc.Nsig if k < 0 else k
+        err = rel_err(logw[c][:, :n], ref["logw"][:, :n])
+        assert err.max() <= 1e-5, (Ls[c], err.max())
+        d, f, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 1e-5, nwl=n)
+        assert not bad, bad[:3]
+        stats.append((d, f))
+        assert np.all(np.isfinite(logw[c]))
+    lat.close()
+    return stats
+
+
+@pytest.mark.parametrize("L,beta,dtau,fill,nwl", [
+    (48, 0.3, 0.05, 0.5, 12),     # M = 6
+    (48, 0.25, 0.05, 1.0, 8),     # M = 5
+    (64, 0.2, 0.05, 1.0, 6),      # M = 4
+    (64, 0.15, 0.05, 0.5, 6),     # M = 3
+    (128, 0.15, 0.05, 0.25, 3),   # M = 3
+    (128, 0.2, 0.05, 0.125, 2),   # M = 4
+])
+def test_wide_first_sweep_parity(L, beta, dtau, fill, nwl):
+    run_case([L, L], [(1.0, 4.0, beta, dtau, fill)] * 2, [21, 22], [nwl, nwl])
+
+
+def test_wide_in_a_ragged_batch():
+    """L = 8, 48, 16, 64 chains in one context (config-3-like mix of sizes, fillings, U)."""
+    Ls = [8, 48, 16, 64]
+    pars = [(1.0, 4.0, 0.5, 0.05, 0.875), (1.0, 8.0, 0.3, 0.05, 0.875), (1.0, 2.0, 0.4, 0.05, 0.5),
+            (1.0, 4.0, 0.2, 0.05, 1.0)]
+    run_case(Ls, pars, [30, 31, 32, 33], [-1, 6, -1, 4])
+
+
+@pytest.mark.parametrize("L", [48, 64, 128])
+def test_wide_gibbs_follows_the_rule(L):
+    """After one sweep, every field value equals the Hirsch-Gibbs rule applied to the GPU's
+    own new worldlines: s = +1 iff u < 1/(1 + exp(-2 lambda m)), u from Philox phase 1."""
+    from paper_2510_13866_gb300 import Lattice
+
+    params = (1.0, 4.0, 0.15, 0.05, 0.25)
+    lat = Lattice(L, [5], precision="fp32")
+    lat.set_params(*params)
+    lat.sweep(1)
+    s, x, _, _ = lat.get_state(0)
+    M, N = s.shape
+    hist = np.zeros((2, M, N), dtype=np.int64)
+    for sg in range(2):
+        for p in range(x.shape[1]):
+            np.add.at(hist[sg], (np.arange(M), x[sg, p]), 1)
+    m = hist[0] - hist[1]
+    lam = oracle.lam(params[1], params[3])
+    ls, xs = np.nonzero(np.ones((M, N), dtype=bool))
+    rng = np.random.default_rng(0)
+    pick = rng.choice(M * N, size=min(M * N, 3000), replace=False)
+    for k in pick:
+        l, xx = int(ls[k]), int(xs[k])
+        u = oracle.uniform(5, 0, 1, l, xx)
+        want = 1 if u < 1.0 / (1.0 + np.exp(-2.0 * lam * m[l, xx])) else -1
+        assert s[l, xx] == want, (l, xx, m[l, xx])
+    lat.close()
+
+
+def test_wide_rejects_fp64_and_adjoint():
+    from paper_2510_13866_gb300 import HQMCError, Lattice
+
+    with pytest.raises(HQMCError):
+        Lattice(64, [0], precision="fp64")
+    lat = Lattice(48, [0], precision="fp32")
+    lat.set_params(1.0, 4.0, 0.1, 0.05, 0.5)
+    with pytest.raises(HQMCError):
+        lat.log_weight_grad()
+    lat.close()
