@@ -96,8 +96,29 @@ int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
 /* Launch configuration: use_graph = replay one captured CUDA graph per sweep;
  * persistent = size the FFBS grid to the resident capacity (each worldline group
  * loops over pairs) instead of one group per pair; warps_per_cta in {1,2,4,8}
- * (0 = default).  Takes effect at the next sweep.  Errors: HQMC_ERR_ARG. */
+ * (0 = default).  Takes effect at the next sweep; a change of grid or shape re-lays
+ * the context out as described at hqmc_set_class_launch.  Errors: HQMC_ERR_ARG. */
 int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
+
+/* Warps per CTA of the FFBS kernel for the chains of lattice size L only (0 = the
+ * context default); wide sizes (L > 32, one CTA per pair) have a fixed shape and ignore
+ * it.  A change of shape re-lays the context out at its next use: fields, worldlines and
+ * the sweep counter are kept, observable accumulators restart, and a workspace attached
+ * by the caller must be attached again (hqmc_workspace_size gives the new size).
+ * Errors: HQMC_ERR_ARG (no chain of size L, bad shape), HQMC_ERR_CUDA. */
+int hqmc_set_class_launch(hqmc_ctx *ctx, int L, int warps_per_cta);
+
+/* Effective warps per CTA for size L (0 for wide sizes).  Errors: HQMC_ERR_ARG. */
+int hqmc_get_class_launch(hqmc_ctx *ctx, int L, int *warps_per_cta);
+
+/* Autotuner of the CTA shape: for every register-line lattice size in the context, time
+ * trial_sweeps sweeps of a temporary copy of that size's chains (same parameters, seeds
+ * and precision; its own cudaMalloc'd workspace, destroyed afterwards) with 1, 2, 4 and
+ * 8 warps per CTA, and keep the fastest with hqmc_set_class_launch.  The context's own
+ * chains are not advanced.  Launch shapes give bitwise-identical results; only speed
+ * changes.  *n_tuned (nullable) receives the number of sizes tuned.
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA. */
+int hqmc_autotune(hqmc_ctx *ctx, int trial_sweeps, int *n_tuned);
 
 /* Device memory the context needs (state + scratch), in bytes, for the current
  * parameters and launch configuration.  Errors: HQMC_ERR_STATE before set_params. */

@@ -101,6 +101,15 @@ struct hqmc_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
+    // per-size CTA shape (warps per CTA) chosen by hqmc_set_class_launch / hqmc_autotune
+    std::vector<std::pair<int, int>> class_wpc;
+    // state kept across a re-layout (launch shape change): restored by the next prepare()
+    bool pending_restore = false;
+    std::vector<uint32_t> keep_bits;
+    std::vector<int16_t> keep_x;
+    unsigned long long keep_sweep = 0;
+    bool keep_started = false;
+
     // adjoint: checkpoint stride (0 = ceil(sqrt M)) and format, context-owned scratch
     int ckpt_stride = 0;
     int ckpt_kind = HQMC_CKPT_BF16;
@@ -270,6 +279,8 @@ int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
 }
 
 int default_wpc(hqmc_ctx *c, int L) {
+    for (auto &kv : c->class_wpc)
+        if (kv.first == L && kv.second > 0) return kv.second;
     if (c->wpc > 0) return c->wpc;
     return c->precision == HQMC_FP64 ? 4 : 4;
 }
@@ -464,6 +475,39 @@ int prepare(hqmc_ctx *c) {
     c->sweeps_host = 0;
     c->ready = true;
     c->started = false;
+    if (c->pending_restore) {
+        HQMC_CUDA(c, cudaMemcpy(c->st.sbits, c->keep_bits.data(), c->keep_bits.size() * 4, cudaMemcpyHostToDevice));
+        HQMC_CUDA(c, cudaMemcpy(c->st.x, c->keep_x.data(), c->keep_x.size() * 2, cudaMemcpyHostToDevice));
+        HQMC_CUDA(c, cudaMemcpy(c->st.sweep, &c->keep_sweep, 8, cudaMemcpyHostToDevice));
+        c->sweeps_host = c->keep_sweep;
+        c->started = c->keep_started;
+        c->pending_restore = false;
+    }
+    return HQMC_OK;
+}
+
+// Keep the chain state (fields, worldlines, sweep counter) on the host and release the
+// layout; the next prepare() lays the context out again and restores it.  Observable
+// accumulators restart from zero.
+int stash_state(hqmc_ctx *c) {
+    if (!c->ready) {
+        free_layout(c);
+        return HQMC_OK;
+    }
+    size_t sb = 0, xb = 0;
+    for (auto &d : c->cdev) {
+        sb += 2ull * d.M * d.L * d.wpl;
+        xb += 2ull * d.Nsig * d.M;
+    }
+    c->keep_bits.resize(sb);
+    c->keep_x.resize(xb);
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    HQMC_CUDA(c, cudaMemcpy(c->keep_bits.data(), c->st.sbits, sb * 4, cudaMemcpyDeviceToHost));
+    HQMC_CUDA(c, cudaMemcpy(c->keep_x.data(), c->st.x, xb * 2, cudaMemcpyDeviceToHost));
+    HQMC_CUDA(c, cudaMemcpy(&c->keep_sweep, c->st.sweep, 8, cudaMemcpyDeviceToHost));
+    c->keep_started = c->started;
+    c->pending_restore = true;
+    free_layout(c);
     return HQMC_OK;
 }
 
@@ -678,32 +722,93 @@ int hqmc_set_launch(hqmc_ctx *c, int use_graph, int persistent, int warps_per_ct
     c->persistent = persistent != 0;
     c->wpc = warps_per_cta;
     drop_graph(c);
-    if (relayout && c->ready) {
-        // the scratch size depends on the grid: rebuild the layout but keep the state
-        std::vector<int8_t> s_save;
-        std::vector<uint32_t> bits;
-        std::vector<int16_t> xs;
-        size_t sb = 0, xb = 0;
-        for (auto &d : c->cdev) {
-            sb += 2ull * d.M * d.L * d.wpl;
-            xb += 2ull * d.Nsig * d.M;
+    // the scratch size depends on the grid: lay out again at the next use, keeping the state
+    if (relayout) return stash_state(c);
+    return HQMC_OK;
+}
+
+int hqmc_set_class_launch(hqmc_ctx *c, int L, int warps_per_cta) {
+    if (!c) return HQMC_ERR_ARG;
+    if (warps_per_cta != 0 && warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
+        return fail(c, HQMC_ERR_ARG, "warps_per_cta must be 0, 1, 2, 4 or 8");
+    bool found = false;
+    for (auto &h : c->ch) found = found || h.L == L;
+    if (!found) return fail(c, HQMC_ERR_ARG, "no chain of this lattice size");
+    const int before = default_wpc(c, L);
+    bool set = false;
+    for (auto &kv : c->class_wpc)
+        if (kv.first == L) {
+            kv.second = warps_per_cta;
+            set = true;
         }
-        bits.resize(sb);
-        xs.resize(xb);
-        unsigned long long sw = 0;
-        HQMC_CUDA(c, cudaMemcpy(bits.data(), c->st.sbits, sb * 4, cudaMemcpyDeviceToHost));
-        HQMC_CUDA(c, cudaMemcpy(xs.data(), c->st.x, xb * 2, cudaMemcpyDeviceToHost));
-        HQMC_CUDA(c, cudaMemcpy(&sw, c->st.sweep, 8, cudaMemcpyDeviceToHost));
-        const bool started = c->started;
-        free_layout(c);
-        int rc = prepare(c);
+    if (!set) c->class_wpc.push_back({L, warps_per_cta});
+    drop_graph(c);
+    if (default_wpc(c, L) != before) return stash_state(c);
+    return HQMC_OK;
+}
+
+int hqmc_get_class_launch(hqmc_ctx *c, int L, int *warps_per_cta) {
+    if (!c || !warps_per_cta) return HQMC_ERR_ARG;
+    *warps_per_cta = L > 32 ? 0 : default_wpc(c, L);
+    return HQMC_OK;
+}
+
+int hqmc_autotune(hqmc_ctx *c, int trial_sweeps, int *n_tuned) {
+    if (!c || trial_sweeps < 1) return HQMC_ERR_ARG;
+    for (auto &h : c->ch)
+        if (!h.set) return fail(c, HQMC_ERR_STATE, "set_params has not been called for every chain");
+    std::vector<int> sizes;
+    for (auto &h : c->ch)
+        if (h.L <= 32 && std::find(sizes.begin(), sizes.end(), h.L) == sizes.end()) sizes.push_back(h.L);
+    int tuned = 0;
+    for (int L : sizes) {
+        // a throwaway context with this size's chains: same parameters, seeds and precision
+        std::vector<int> Ls;
+        std::vector<uint64_t> seeds;
+        std::vector<const HostChain *> hs;
+        for (auto &h : c->ch)
+            if (h.L == L) {
+                Ls.push_back(h.L);
+                seeds.push_back(h.seed);
+                hs.push_back(&h);
+            }
+        hqmc_ctx *t = nullptr;
+        int rc = hqmc_init_lattice(&t, int(Ls.size()), Ls.data(), seeds.data(), c->precision, c->device);
+        if (rc) return fail(c, rc, "autotune: temporary context");
+        for (size_t i = 0; i < hs.size(); ++i) {
+            rc = hqmc_set_params(t, int(i), hs[i]->t, hs[i]->U, hs[i]->beta, hs[i]->dtau, hs[i]->filling);
+            if (rc) break;
+        }
+        int best = 0;
+        float best_ms = 0.f;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = HQMC_ERR_CUDA;
+        for (int w : {1, 2, 4, 8}) {
+            if (rc) break;
+            rc = hqmc_set_launch(t, c->use_graph ? 1 : 0, c->persistent ? 1 : 0, w);
+            if (!rc) rc = hqmc_sweep(t, 2, nullptr);  // warm-up (and graph capture)
+            if (rc) break;
+            cudaEventRecord(e0, t->stream);
+            rc = hqmc_sweep(t, trial_sweeps, nullptr);
+            cudaEventRecord(e1, t->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = HQMC_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && (best == 0 || ms < best_ms)) {
+                best = w;
+                best_ms = ms;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        const std::string detail = t->err;
+        hqmc_destroy(t);
+        if (rc) return fail(c, rc, "autotune: " + detail);
+        rc = hqmc_set_class_launch(c, L, best);
         if (rc) return rc;
-        HQMC_CUDA(c, cudaMemcpy(c->st.sbits, bits.data(), sb * 4, cudaMemcpyHostToDevice));
-        HQMC_CUDA(c, cudaMemcpy(c->st.x, xs.data(), xb * 2, cudaMemcpyHostToDevice));
-        HQMC_CUDA(c, cudaMemcpy(c->st.sweep, &sw, 8, cudaMemcpyHostToDevice));
-        c->sweeps_host = sw;
-        c->started = started;
+        ++tuned;
     }
+    if (n_tuned) *n_tuned = tuned;
     return HQMC_OK;
 }
 
@@ -727,7 +832,7 @@ int hqmc_workspace_size(hqmc_ctx *c, size_t *bytes) {
 int hqmc_attach_workspace(hqmc_ctx *c, void *dev_ptr, size_t bytes) {
     if (!c || !dev_ptr) return HQMC_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(c, HQMC_ERR_ARG, "workspace must be 256-byte aligned");
-    free_layout(c);
+    free_layout(c);  // a stashed state (after a launch-shape change) is restored by prepare()
     c->attached = static_cast<unsigned char *>(dev_ptr);
     c->attached_bytes = bytes;
     size_t need = 0;

@@ -26,6 +26,9 @@ SIGNATURES = {
     "hqmc_set_params": (_i, [_vp, _i, _d, _d, _d, _d, _d]),
     "hqmc_set_stream": (_i, [_vp, _vp]),
     "hqmc_set_launch": (_i, [_vp, _i, _i, _i]),
+    "hqmc_set_class_launch": (_i, [_vp, _i, _i]),
+    "hqmc_get_class_launch": (_i, [_vp, _i, _vp]),
+    "hqmc_autotune": (_i, [_vp, _i, _vp]),
     "hqmc_workspace_size": (_i, [_vp, C.POINTER(_sz)]),
     "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
@@ -144,6 +147,50 @@ class Lattice:
         self._check(lib().hqmc_set_launch(self._ctx, int(use_graph), int(persistent), int(warps_per_cta)))
         if self.torch_memory and self._ws is not None:
             self._attach()
+
+    def set_class_launch(self, L, warps_per_cta):
+        self._check(lib().hqmc_set_class_launch(self._ctx, int(L), int(warps_per_cta)))
+        if self.torch_memory and self._ws is not None:
+            self._attach()
+
+    def class_launch(self, L):
+        w = C.c_int(0)
+        self._check(lib().hqmc_get_class_launch(self._ctx, int(L), C.byref(w)))
+        return w.value
+
+    def autotune(self, trial_sweeps=3, cache=None):
+        """CTA shape per lattice size, timed by the library on throwaway copies of the chains
+        (hqmc_autotune).  With `cache` (a JSON path) the choice is keyed by GPU, precision,
+        size, slices and pair count, read from the file when present and written back."""
+        import json
+
+        key_of = {}
+        for L in sorted(set(int(v) for v in self.Ls)):
+            if L > 32:
+                continue
+            shp = [s for s, l in zip(self._shapes(), self.Ls) if l == L]
+            Mmax = max(M for _, M, _ in shp)
+            pairs = sum(2 * ((ns + 1) // 2) for _, _, ns in shp)
+            name = self._torch.cuda.get_device_name(self.device)
+            key_of[L] = f"{name}|{'fp64' if self.precision == HQMC_FP64 else 'fp32'}|L={L}|M={Mmax}|pairs={pairs}"
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        if all(k in table for k in key_of.values()):
+            for L, k in key_of.items():
+                self.set_class_launch(L, table[k])
+            return {L: table[k] for L, k in key_of.items()}
+        n = C.c_int(0)
+        self._check(lib().hqmc_autotune(self._ctx, int(trial_sweeps), C.byref(n)))
+        if self.torch_memory and self._ws is not None:
+            self._attach()
+        chosen = {L: self.class_launch(L) for L in key_of}
+        if cache:
+            table.update({key_of[L]: w for L, w in chosen.items()})
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return chosen
 
     def workspace_size(self):
         n = C.c_size_t(0)
