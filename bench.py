@@ -142,6 +142,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+WORKLOADS = {
+    "L32": "config 2 (the headline): " + WORKLOAD,
+    "ragged": ("256 ragged chains, L in {8,12,16,24,32,48}, beta in {2,4,6}, U in {2,4,8}, filling in "
+               "{0.5,0.875,1}, dtau=0.05, drawn per chain from Philox key (1,0); one graph replay per sweep"),
+    "L64": "2D Hubbard L=64 (N=4096) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
+    "L128": "2D Hubbard L=128 (N=16384) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
+}
+
+
+def workload(name, rank, chains):
+    """(L per chain, params per chain, seeds) of a named workload on rank `rank`."""
+    from paper_2510_13866_gb300.shard import chain_seeds
+    from paper_2510_13866_gb300.workloads import ragged
+
+    if name == "L32":
+        n = chains
+        p = (WORK["t"], WORK["U"], WORK["beta"], WORK["dtau"], WORK["filling"])
+        return [32] * n, [p] * n, chain_seeds(rank, n)
+    if name == "ragged":
+        n = chains if chains != WORK["chains"] else 256
+        work = ragged(n)
+        return [w[0] for w in work], [w[1] for w in work], chain_seeds(rank, n)
+    L = int(name[1:])
+    n = chains if chains != WORK["chains"] else 16
+    return [L] * n, [(1.0, 4.0, 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
+
+
+def kernel_source_digest():
+    """Digest of the FFBS kernel sources: the committed DRAM counters apply only to it."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("ffbs.cuh", "ffbs_big.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2510_13866_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -150,8 +188,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS),
+                    help="L32 (default, the headline configuration), ragged, L64, L128")
     ap.add_argument("--chains", type=int, default=WORK["chains"],
-                    help="chains per GPU (default 64; smaller values only for profiling captures)")
+                    help="chains per GPU (default: the workload's own; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -181,15 +221,23 @@ def main():
         return float(t.item())
 
     from paper_2510_13866_gb300 import Lattice
-    from paper_2510_13866_gb300.shard import chain_seeds
 
-    w = dict(WORK)
-    w["chains"] = args.chains
-    seeds = chain_seeds(rank, w["chains"])
-    lat = Lattice(w["L"], seeds, precision="fp32", device=local)
-    lat.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
-    lat.prepare()
-    L, M, Ns = lat.shapes[0]
+    Ls, pars, seeds = workload(args.workload, rank, args.chains)
+    nchains = len(Ls)
+
+    def make(precision):
+        lt = Lattice(Ls, seeds, precision=precision, device=local)
+        if len(set(pars)) == 1:
+            lt.set_params(*pars[0])
+        else:
+            for c, p in enumerate(pars):
+                lt.set_params(*p, chain=c)
+        lt.prepare()
+        return lt
+
+    lat = make("fp32")
+    shapes = lat.shapes
+    nclasses = len(set(Ls))
     stream = torch.cuda.current_stream(local)
     lat.sweep(args.warmup)
     torch.cuda.synchronize()
@@ -211,32 +259,49 @@ def main():
     ms = max_over_ranks(ms)
     value = world * args.steps / (ms / 1e3)
 
-    # FFBS kernel time from events around its launches (same K sweeps, no graph)
+    # FFBS kernel time from CUDA events around its launches on the launching streams
+    # (same sweeps, plain launches)
     lat.set_profiling(args.steps)
     lat.sweep(args.steps)
     ffbs_ms, slice_ms, nprof = lat.profile_read()
     lat.set_profiling(0)
     ffbs_avg = ffbs_ms / max(1, nprof)
     slice_avg = slice_ms / max(1, nprof)
-    part_slices = w["chains"] * 2 * Ns * M
-    alg_bytes = part_slices * 8.0 * L * L          # f_l written (4N B) and read back (4N B)
-    alg_flops = part_slices * (5.0 * L * L * np.log2(L * L) + 4.0 * L * L)
+    # algorithmic work per launch: every particle-slice writes f_l (4N B) and reads it back
+    # (4N B); 5 N log2 N + 4 N flops
+    part_slices = sum(2 * ns * M for (_, M, ns) in shapes)
+    alg_bytes = sum(2 * ns * M * 8.0 * L * L for (L, M, ns) in shapes)
+    alg_flops = sum(2 * ns * M * (5.0 * L * L * np.log2(L * L) + 4.0 * L * L) for (L, M, ns) in shapes)
     hbm_peak, peak_src, sm_max = peaks()
     achieved = alg_bytes / (ffbs_avg / 1e3) / 1e9
     alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
     achieved_flops = alg_flops / (ffbs_avg / 1e3) / 1e12
-    traffic = None
+    traffic, traffic_note = None, "no committed DRAM counters for this workload"
     tp = os.path.join(ROOT, "profiles", "ffbs_traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get("bytes_per_launch")
+            rec = json.load(open(tp)).get(args.workload)
+            if rec and rec.get("kernel_digest") == kernel_source_digest():
+                traffic = rec["bytes_per_launch"] * (nchains / rec["chains"])
+                traffic_note = rec["how"]
+            elif rec:
+                traffic_note = "kernel changed since the committed DRAM counters were taken"
         except Exception:
             traffic = None
+    kname = "ffbs_kernel<float,32>" if args.workload == "L32" else "FFBS launches (all sizes)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
-                "kernel": "ffbs_kernel<float,32>", "kernel_ms": ffbs_avg, "gibbs_measure_ms": slice_avg,
+                "frac": achieved / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
+                "peak_source": peak_src, "kernel": kname, "kernel_ms": ffbs_avg, "gibbs_measure_ms": slice_avg,
+                "alg_bytes_per_launch": alg_bytes,
                 "alu": {"achieved_tflops": achieved_flops, "peak_tflops": alu_peak,
                         "frac": achieved_flops / alu_peak}}
+
+    # FP32 diagnostics over the sweeps run so far (degenerate draws are counted, not raised)
+    obs = lat.measure(reset=True)
+    n_sw = max(1, obs[0]["n_samples"])
+    diag = {"degenerate_per_sweep": sum(o["n_degenerate"] for o in obs) / n_sw,
+            "nonpositive_per_sweep": sum(o["n_nonpositive"] for o in obs) / n_sw,
+            "draws_per_sweep": sum(2 * ns * (M - 1) for (_, M, ns) in shapes)}
 
     # end to end through the public API: host log-weight buffer every step
     ke = min(args.steps, 20)
@@ -247,14 +312,13 @@ def main():
     te = time.perf_counter() - t0
     e2e_val = max_over_ranks(te)
     e2e = {"value": world * ke / e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": int(8 * w["chains"] * 2 * Ns) + 4}
+           "d2h_bytes_per_step": int(8 * sum(2 * ns for (_, _, ns) in shapes)) + 4}
     lat.close()
 
     # plain FP64 form: same kernels in double, one launch per phase, no graph
     fp64 = None
-    if args.fp64_steps > 0:
-        lat64 = Lattice(w["L"], seeds, precision="fp64", device=local)
-        lat64.set_params(w["t"], w["U"], w["beta"], w["dtau"], w["filling"])
+    if args.fp64_steps > 0 and max(Ls) <= 32:
+        lat64 = make("fp64")
         lat64.sweep(1)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -267,20 +331,24 @@ def main():
         lat64.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "L32":
         cpu = cpu_oracle_sample()
 
     if rank == 0:
-        wl = WORKLOAD if w["chains"] == WORK["chains"] else WORKLOAD.replace("x 64 chains", f"x {w['chains']} chains")
+        wl = WORKLOADS[args.workload]
+        if args.workload == "L32" and nchains != WORK["chains"]:
+            wl = wl.replace("x 64 chains", f"x {nchains} chains")
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl, "L": L, "M": M, "chains_per_gpu": w["chains"],
-                           "worldlines_per_chain": 2 * Ns, "parallelism": f"chains sharded over {world} GPU(s)",
-                           "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2"},
+                "config": {"workload": wl, "L": sorted(set(Ls)) if nclasses > 1 else Ls[0],
+                           "M": sorted(set(M for _, M, _ in shapes)) if nclasses > 1 else shapes[0][1],
+                           "chains_per_gpu": nchains, "parallelism": f"chains sharded over {world} GPU(s)",
+                           "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2; no flush needed"},
                 "particle_slice_updates_per_s": value * part_slices,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * 3, "clocks": clocks, "fp64_plain": fp64}
+                "gpu_launches": args.steps * (nclasses + 2), "clocks": clocks, "fp64_plain": fp64,
+                "fp32_diagnostics": diag}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -65,6 +65,14 @@ typedef struct {
     double m2;         /* <(n_up - n_dn)^2> = 4 <(S^z)^2> */
     double ekin;       /* -(t/beta) <sum over links d/dt log G(x_{l+1} - x_l)> / N */
     double s_pipi;     /* S(k) at k = (pi, pi) (nearest grid point for odd L) */
+    /* FFBS diagnostics since the last reset (not errors; a sweep continues):
+     * n_degenerate   draws whose CDF was all zero (the worldline keeps its site at that
+     *                slice) plus forward slices with a non-finite normaliser -- in FP32 this
+     *                happens where a path sits in a region whose true weight lies below the
+     *                FFT's rounding floor (about 1e-7 of the slice maximum);
+     * n_nonpositive  filter amplitudes alpha_M(x_a) <= 0 (that log-weight is not finite). */
+    int64_t n_degenerate;
+    int64_t n_nonpositive;
 } hqmc_obs;
 
 /* Create a context for n_chains independent chains on CUDA device `device`.
@@ -136,7 +144,8 @@ int hqmc_attach_workspace(hqmc_ctx *ctx, void *dev_ptr, size_t bytes);
  * [2][Nsig] (spin-major), where Z_p = sum over closed paths of worldline p with its
  * anchor-slice position held of prod_l W_l(x_l) G(x_{l+1} - x_l), evaluated with the
  * field before that sweep's Gibbs step.  The call blocks until the sweeps finish.
- * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
+ * Numerical degeneracies are counted (hqmc_obs.n_degenerate, n_nonpositive), not raised.
+ * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_TIMEOUT. */
 int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
 
 /* Read the accumulated observables.  out: host array [n_chains] (nullable).

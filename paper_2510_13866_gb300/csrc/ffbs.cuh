@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (i < M - 1) {
                 int e0 = 0, e1 = 0;
                 if (s0 > T(0) && s0 < T(1e30)) e0 = fbits<T>::exponent(s0);
-                else if (gl == 0) atomicOr(st.status, kStatusDegenerate);
+                else if (gl == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
                 if (s1 > T(0) && s1 < T(1e30)) e1 = fbits<T>::exponent(s1);
                 esum0 += e0;
                 esum1 += e1;
@@ -259,10 +259,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             const double ln2 = 0.69314718055994530942;
             const double lz0 = double(esum0) * ln2 + log(double(fin0));
             st.logw[cd.logw_off + wl0] = lz0;
-            if (!(fin0 > T(0))) atomicOr(st.status, kStatusNonPositive);
+            if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1) {
                 st.logw[cd.logw_off + wl1] = double(esum1) * ln2 + log(double(fin1));
-                if (!(fin1 > T(0))) atomicOr(st.status, kStatusNonPositive);
+                if (!(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             }
         }
 
@@ -415,13 +415,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 }
                 if (row0 < 0 || !(S0 > T(0))) {
                     nxt0 = cur0;  // all-zero CDF: stay and report
-                    if (gl == 0) atomicOr(st.status, kStatusDegenerate);
+                    if (gl == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
                 } else {
                     nxt0 = col0 + L * row0;
                 }
                 if (row1 < 0 || !(S1 > T(0))) {
                     nxt1 = cur1;
-                    if (gl == 0 && has1) atomicOr(st.status, kStatusDegenerate);
+                    if (gl == 0 && has1) atomicAdd(&st.meas[c].degenerate, 1ull);
                 } else {
                     nxt1 = col1 + L * row1;
                 }

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, 1) ffbs_big_kernel(DevState st,
             if (i < M - 1) {
                 int e0 = 0, e1 = 0;
                 if (s0 > T(0) && s0 < T(1e30)) e0 = fbits<T>::exponent(s0);
-                else if (tid == 0) atomicOr(st.status, kStatusDegenerate);
+                else if (tid == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
                 if (s1 > T(0) && s1 < T(1e30)) e1 = fbits<T>::exponent(s1);
                 esum0 += e0;
                 esum1 += e1;
@@ -318,10 +318,10 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, 1) ffbs_big_kernel(DevState st,
         if (tid == 0) {
             const double ln2 = 0.69314718055994530942;
             st.logw[cd.logw_off + wl0] = double(esum0) * ln2 + log(double(fin0));
-            if (!(fin0 > T(0))) atomicOr(st.status, kStatusNonPositive);
+            if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1) {
                 st.logw[cd.logw_off + wl1] = double(esum1) * ln2 + log(double(fin1));
-                if (!(fin1 > T(0))) atomicOr(st.status, kStatusNonPositive);
+                if (!(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             }
         }
 
@@ -463,14 +463,14 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, 1) ffbs_big_kernel(DevState st,
             int nxt0, nxt1;
             if (win0 < 0 || !(Stot.x > T(0))) {
                 nxt0 = cur0;
-                if (tid == 0) atomicOr(st.status, kStatusDegenerate);
+                if (tid == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
             } else {
                 const int kk = win0 >> 8, col = (kk % S) * E + (win0 & 255);
                 nxt0 = col + L * (kk / S);
             }
             if (win1 < 0 || !(Stot.y > T(0))) {
                 nxt1 = cur1;
-                if (tid == 0 && has1) atomicOr(st.status, kStatusDegenerate);
+                if (tid == 0 && has1) atomicAdd(&st.meas[c].degenerate, 1ull);
             } else {
                 const int kk = win1 >> 8, col = (kk % S) * E + (win1 & 255);
                 nxt1 = col + L * (kk / S);

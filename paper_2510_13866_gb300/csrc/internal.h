@@ -55,7 +55,10 @@ struct MeasAcc {
     unsigned long long m2_sum;  // sum m^2
     unsigned long long samples; // sweeps accumulated
     double link_sum;            // sum over worldlines and links of d/dt log G
-    double pad[3];
+    unsigned long long degenerate;   // FFBS draws that met an all-zero CDF (the site was kept)
+                                     // and forward slices with a non-finite normaliser
+    unsigned long long nonpositive;  // filter amplitudes alpha_M(x_a) <= 0 (log-weight invalid)
+    double pad[1];
 };
 
 struct DevState {
@@ -114,7 +117,7 @@ cudaError_t ffbs_occupancy(int L, bool fp64, int warps_per_cta, int *blocks_per_
 bool ffbs_supported(int L);
 
 cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stream);
-cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int slices_per_cta,
+cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int slices_per_cta,
                          bool measure, cudaStream_t stream);
 cudaError_t configure_slice();
 void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);

@@ -238,10 +238,13 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     const long long nx = 2LL * Nsig * M;
     static_unpack_kernel<<<152, 256, 0, st>>>(base, lay, nx, x);
     if (cudaGetLastError() != cudaSuccess) return HQMC_ERR_CUDA;
+    MeasAcc acc{};
     if (cudaMemcpyAsync(&status, base + lay.status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HQMC_ERR_CUDA;
+    if (cudaMemcpyAsync(&acc, base + lay.meas, sizeof(MeasAcc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HQMC_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HQMC_ERR_CUDA;
     if (status & kStatusTimeout) return HQMC_ERR_TIMEOUT;
-    if (status) return HQMC_ERR_NUMERIC;
+    if (status || acc.degenerate || acc.nonpositive) return HQMC_ERR_NUMERIC;
     return HQMC_OK;
 }
 #pragma GCC visibility pop

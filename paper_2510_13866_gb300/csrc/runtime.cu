@@ -560,7 +560,9 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     int max_M = 0;
     for (auto &d : c->cdev) max_M = std::max(max_M, d.M);
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[2], st));
-    cudaError_t e = launch_slice(c->st, c->nchains, max_M, 8, true, st);
+    int max_L = 0;
+    for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
+    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, 8, true, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
     if (prof) {
         HQMC_CUDA(c, cudaEventRecord(pe[3], st));
@@ -911,6 +913,8 @@ int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) 
             o.ekin = ns > 0 ? -(c->ch[i].t / c->ch[i].beta) * acc[i].link_sum / (ns * d.N) : 0.0;
             const int kh = d.L / 2;
             o.s_pipi = skh[d.meas_off + kh + d.L * kh];
+            o.n_degenerate = (int64_t)acc[i].degenerate;
+            o.n_nonpositive = (int64_t)acc[i].nonpositive;
         }
     }
     if (reset) {

@@ -9,7 +9,8 @@ namespace hqmc {
 namespace {
 
 constexpr int kSliceThreads = 256;
-constexpr int kSkSmemMaxN = 4096;  // S(k) accumulated in shared memory up to L = 64
+constexpr int kSkSmemMaxN = 4096;  // S(k) summed over the CTA's slices in shared memory up
+                                   // to L = 64; beyond, each slice adds to global memory
 
 // Block-wide sum of an unsigned 64-bit value into *dst (one atomic per block).
 __device__ void block_add_u64(unsigned long long v, unsigned long long *dst, unsigned long long *red) {
@@ -39,15 +40,10 @@ __host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl) {
     s.rows = 0;
     s.red = align16(s.rows + 2 * size_t(L) * wpl * 4);
     s.ms = align16(s.red + 32 * 8);
-    if (N <= size_t(kSkSmemMaxN)) {
-        s.x1 = align16(s.ms + N * 4);
-        s.tw = align16(s.x1 + N * 8);
-        s.sk = align16(s.tw + size_t(L) * 8);
-        s.total = align16(s.sk + N * 8);
-    } else {
-        s.x1 = s.tw = s.sk = s.ms;
-        s.total = s.ms;
-    }
+    s.x1 = align16(s.ms + N * 4);
+    s.tw = align16(s.x1 + N * 8);
+    s.sk = align16(s.tw + size_t(L) * 8);
+    s.total = N <= size_t(kSkSmemMaxN) ? align16(s.sk + N * 8) : s.sk;
     return s;
 }
 
@@ -70,7 +66,8 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
     const double lam = cd.lam;
     const ChainTab &tb = st.tabs[c];
 
-    const bool do_sk = measure && N <= kSkSmemMaxN;
+    const bool do_sk = measure != 0;
+    const bool sk_smem = N <= kSkSmemMaxN;
     const SliceSmem lay = slice_smem_layout(L, wpl);
     uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
     uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
@@ -87,7 +84,8 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
             sincospif(2.0f * float(j) / float(L), &s, &co);
             tw[j] = make_float2(co, -s);
         }
-        for (int k = threadIdx.x; k < N; k += blockDim.x) skacc[k] = 0.0;
+        if (sk_smem)
+            for (int k = threadIdx.x; k < N; k += blockDim.x) skacc[k] = 0.0;
     }
     __syncthreads();
 
@@ -163,7 +161,9 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
                     ph += ky;
                     if (ph >= L) ph -= L;
                 }
-                skacc[o] += double(re * re + im * im) / double(N);
+                const double v = double(re * re + im * im) / double(N);
+                if (sk_smem) skacc[o] += v;
+                else atomicAdd(&st.sk[cd.meas_off + o], v);
             }
         }
         __syncthreads();
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
         block_add_u64(d_acc, &acc.d_sum, red);
         block_add_u64(m2_acc, &acc.m2_sum, red);
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&acc.samples, 1ull);
-        if (do_sk)
+        if (do_sk && sk_smem)
             for (int k = threadIdx.x; k < N; k += blockDim.x) atomicAdd(&st.sk[cd.meas_off + k], skacc[k]);
     }
 }
@@ -193,9 +193,9 @@ cudaError_t configure_slice() {
     return cudaFuncSetAttribute(slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slice_smem_max()));
 }
 
-cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int slices_per_cta, bool measure,
+cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int slices_per_cta, bool measure,
                          cudaStream_t stream) {
-    const size_t sm = slice_smem_max();
+    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32).total;
     dim3 grid((max_M + slices_per_cta - 1) / slices_per_cta, nchains);
     slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, slices_per_cta, measure ? 1 : 0);
     return cudaGetLastError();

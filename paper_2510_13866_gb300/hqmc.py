@@ -56,7 +56,8 @@ class HQMCError(RuntimeError):
 
 class Obs(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("density", C.c_double), ("double_occ", C.c_double),
-                ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double)]
+                ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double),
+                ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64)]
 
 
 _lib = None
@@ -251,7 +252,8 @@ class Lattice:
             N = L * L
             ob = obs[c]
             res.append(dict(n_samples=ob.n_samples, density=ob.density, double_occ=ob.double_occ, m2=ob.m2,
-                            ekin=ob.ekin, s_pipi=ob.s_pipi, Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
+                            ekin=ob.ekin, s_pipi=ob.s_pipi, n_degenerate=ob.n_degenerate,
+                            n_nonpositive=ob.n_nonpositive, Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
             o += N
         return res
 

@@ -100,3 +100,30 @@ def test_wide_rejects_fp64_and_adjoint():
     with pytest.raises(HQMCError):
         lat.log_weight_grad()
     lat.close()
+
+
+@pytest.mark.parametrize("L", [64, 128])
+def test_wide_measure_matches_oracle_on_gpu_paths(L):
+    """Observables of one sweep against the oracle's definitions applied to the GPU's own
+    new worldlines (S(k) summed in shared memory at L = 64, in global memory at L = 128)."""
+    from paper_2510_13866_gb300 import Lattice
+
+    params = (1.0, 4.0, 0.15, 0.05, 0.25)
+    lat = Lattice(L, [8], precision="fp32")
+    lat.set_params(*params)
+    lat.sweep(1)
+    s, x, _, _ = lat.get_state(0)
+    M, N = s.shape
+    hist = np.zeros((2, M, N), dtype=np.int32)
+    for sg in range(2):
+        for p in range(x.shape[1]):
+            np.add.at(hist[sg], (np.arange(M), x[sg, p]), 1)
+    m = lat.measure()[0]
+    mo = oracle.measure(L, M, hist)
+    assert m["n_samples"] == 1
+    assert m["density"] == pytest.approx(mo["n"] / (M * N), rel=1e-14)
+    assert m["double_occ"] == pytest.approx(mo["d"] / (M * N), rel=1e-14)
+    assert m["m2"] == pytest.approx(mo["m2"] / (M * N), rel=1e-14)
+    assert np.allclose(m["Sk"], mo["Sk"] / (4 * M), rtol=1e-4, atol=1e-5)
+    assert np.allclose(m["Cr"], mo["Cr"] / (4 * M), rtol=1e-4, atol=1e-5)
+    lat.close()
