@@ -41,7 +41,8 @@ struct FfbsGeo {
     static constexpr size_t MIXB = a16(size_t(L) * sizeof(V));
     static constexpr size_t G2B = a16(size_t(2 * L) * sizeof(T));
     static constexpr size_t WXB = a16(size_t(L) * sizeof(V));
-    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB;
+    static constexpr size_t RBB = a16(size_t(2 * L) * sizeof(V));  // crossing rows of both worldlines
+    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB + RBB;
 };
 
 // Target u*S of an inverse-CDF draw from the Philox word w, in the CDF's precision.
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     V *mix = reinterpret_cast<V *>(gsm + G::XBUF);
     T *g2 = reinterpret_cast<T *>(gsm + G::XBUF + G::MIXB);
     V *wx = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B);
+    V *rb = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB);  // [2][L]
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
     const long long ngroups = (long long)gridDim.x * wpc * G::GPW;
     V *slot = reinterpret_cast<V *>(fl.scratch) + gid * fl.slot_elems;
@@ -223,8 +225,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             // v = alpha_{l+1} (scale 2^{-esum}) in the other layout
             V s = vzero(v[0]);
             if (active) {
+                // pairwise (tree) sum: short dependency chains
+                V part[(L + 1) / 2];
 #pragma unroll
-                for (int r = 0; r < L; ++r) s = vadd(s, v[r]);
+                for (int r = 0; r < L / 2; ++r) part[r] = vadd(v[2 * r], v[2 * r + 1]);
+                if constexpr (L % 2) part[L / 2] = v[L - 1];
+#pragma unroll
+                for (int w = 1; w < (L + 1) / 2; w <<= 1)
+#pragma unroll
+                    for (int r = 0; r + w < (L + 1) / 2; r += 2 * w) part[r] = vadd(part[r], part[r + w]);
+                s = part[0];
             }
             T s0 = group_sum<GW>(s.x, gmask);
             T s1 = group_sum<GW>(s.y, gmask);
@@ -366,26 +376,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             const T S1 = __shfl_sync(gmask, in1, L - 1, GW);
             const T t0 = draw_target<T>(uw0, S0);
             const T t1 = draw_target<T>(uw1, S1);
-            // the row that holds the crossing, then the first column whose prefix crosses:
-            // the count of prefixes at or below the lane's remaining threshold
+            // the row that holds the crossing (the first row whose total exceeds what remains
+            // of u*S), then in it the first column whose prefix does: the crossing row's
+            // prefixes go through shared memory, one column per lane
             const T r0 = t0 - ex0, r1 = t1 - ex1;
-            int n0 = 0, n1 = 0;
-            if (active) {
-#pragma unroll
-                for (int ix = 0; ix < L; ++ix) {
-                    n0 += (v[ix].x <= r0) ? 1 : 0;
-                    n1 += (v[ix].y <= r1) ? 1 : 0;
-                }
-            }
             int nxt0, nxt1;
             {
                 const int base = gw * GW;
-                const unsigned b0 = __ballot_sync(gmask, active && t0 >= ex0 && n0 < L) & gmask;
-                const unsigned b1 = __ballot_sync(gmask, active && t1 >= ex1 && n1 < L) & gmask;
+                const unsigned b0 = __ballot_sync(gmask, active && t0 >= ex0 && P.x > r0) & gmask;
+                const unsigned b1 = __ballot_sync(gmask, active && t1 >= ex1 && P.y > r1) & gmask;
                 int row0 = b0 ? __ffs(b0) - 1 - base : -1;
                 int row1 = b1 ? __ffs(b1) - 1 - base : -1;
-                int col0 = __shfl_sync(gmask, n0, row0 < 0 ? 0 : row0, GW);
-                int col1 = __shfl_sync(gmask, n1, row1 < 0 ? 0 : row1, GW);
+                auto put_row = [&](V *d) {
+                    if constexpr (CH == 2) {
+#pragma unroll
+                        for (int j = 0; j < L / 2; ++j)
+                            reinterpret_cast<float4 *>(d)[j] =
+                                make_float4(v[2 * j].x, v[2 * j].y, v[2 * j + 1].x, v[2 * j + 1].y);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < L; ++j) d[j] = v[j];
+                    }
+                };
+                if (active && gl == row0) put_row(rb);
+                if (active && gl == row1) put_row(rb + L);
+                __syncwarp(gmask);
+                const T q0 = __shfl_sync(gmask, r0, row0 < 0 ? 0 : row0, GW);
+                const T q1 = __shfl_sync(gmask, r1, row1 < 0 ? 0 : row1, GW);
+                const unsigned c0 = __ballot_sync(gmask, active && row0 >= 0 && rb[gl].x > q0) & gmask;
+                const unsigned c1 = __ballot_sync(gmask, active && row1 >= 0 && rb[L + gl].y > q1) & gmask;
+                __syncwarp(gmask);
+                int col0 = c0 ? __ffs(c0) - 1 - base : 0;
+                int col1 = c1 ? __ffs(c1) - 1 - base : 0;
                 if (row0 < 0 || row1 < 0) {
                     // u*S at or beyond the rounded total: the last site with a positive weight
                     int last0 = -1, last1 = -1;
