@@ -108,6 +108,11 @@ int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
  * the context out as described at hqmc_set_class_launch.  Errors: HQMC_ERR_ARG. */
 int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
 
+/* Slices of one chain handled by one CTA of the Gibbs/measure kernel (default 8; more
+ * slices per CTA means fewer S(k) partial sums to merge, fewer means more parallelism).
+ * Results do not depend on it.  Errors: HQMC_ERR_ARG (outside 1..1024). */
+int hqmc_set_slice_launch(hqmc_ctx *ctx, int slices_per_cta);
+
 /* Warps per CTA of the FFBS kernel for the chains of lattice size L only (0 = the
  * context default); wide sizes (L > 32, one CTA per pair) have a fixed shape and ignore
  * it.  A change of shape re-lays the context out at its next use: fields, worldlines and

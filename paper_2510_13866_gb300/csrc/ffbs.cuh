@@ -131,7 +131,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     V *slot = reinterpret_cast<V *>(fl.scratch) + gid * fl.slot_elems;
     const uint64_t sweep = *st.sweep;
 
-    for (long long q = gid; q < fl.total_pairs; q += ngroups) {
+    // pairs are taken from a work counter (classes list their chains by decreasing M, so
+    // the longest pairs go first and the tail is short)
+    (void)ngroups;
+    for (;;) {
+        unsigned qn = 0;
+        if (gl == 0) qn = atomicAdd(fl.next_pair, 1u);
+        const long long q = (long long)__shfl_sync(gmask, qn, 0, GW);
+        if (q >= fl.total_pairs) break;
         // ---- locate the pair: chain, spin, worldlines ----
         int lo = 0, hi = fl.nclass - 1;
         while (lo < hi) {

@@ -189,7 +189,13 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, 1) ffbs_big_kernel(DevState st,
         for (int w = 0; w < (L + 31) / 32; ++w) wb[w] = base[((long long)l * L + line) * wpl + w];
     };
 
-    for (long long q = blockIdx.x; q < fl.total_pairs; q += gridDim.x) {
+    // pairs are taken from a work counter, longest chains first
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) ibuf[4] = int(atomicAdd(fl.next_pair, 1u));
+        __syncthreads();
+        const long long q = ibuf[4];
+        if (q >= fl.total_pairs) break;
         int lo = 0, hi = fl.nclass - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

@@ -87,6 +87,7 @@ struct FfbsLaunch {
     int M_max;                 // largest M in the class (scratch slot size)
     void *scratch;             // slots of M_max * L * L complex values
     long long slot_elems;      // complex elements per slot
+    unsigned *next_pair;       // work counter: groups take pairs in order (zeroed per launch)
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.

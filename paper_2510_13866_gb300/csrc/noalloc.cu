@@ -77,6 +77,7 @@ __global__ void static_setup_kernel(unsigned char *base, StaticLayout lay, Chain
         cls[0] = 0;                // chain id
         cls[1] = 0;                // pair offsets [0, 2*npair]
         cls[2] = 2 * cd.npair;
+        cls[3] = 0;                // work counter of the FFBS launch
         *reinterpret_cast<int *>(base + lay.anchor) = -1;
         *reinterpret_cast<unsigned long long *>(base + lay.sweep) = sweep;
         *reinterpret_cast<unsigned *>(base + lay.status) = 0u;
@@ -233,6 +234,7 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     fl.M_max = M;
     fl.scratch = base + lay.slots;
     fl.slot_elems = (long long)M * L * L;
+    fl.next_pair = reinterpret_cast<unsigned *>(base + lay.cls) + 3;
     e = f64 ? launch_ffbs_f64(L, ds, fl, int(grid), wpc, st) : launch_ffbs_f32(L, ds, fl, int(grid), wpc, st);
     if (e != cudaSuccess) return HQMC_ERR_CUDA;
     const long long nx = 2LL * Nsig * M;

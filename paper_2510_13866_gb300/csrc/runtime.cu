@@ -79,6 +79,7 @@ struct hqmc_ctx {
     std::vector<cudaEvent_t> ev;
     bool use_graph = true, persistent = true;
     int wpc = 0;
+    int slices_per_cta = 4;  // Gibbs/measure kernel: slices handled by one CTA
     int num_sms = 0;
     std::string err;
 
@@ -303,6 +304,10 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         }
         it->chains.push_back(i);
     }
+    // within a size class the longest chains (largest M) go first: groups take pairs in
+    // this order from the class's work counter, which keeps the tail of a launch short
+    for (auto &k : c->classes)
+        std::stable_sort(k.chains.begin(), k.chains.end(), [&](int x, int y) { return c->ch[x].M > c->ch[y].M; });
     size_t off = 0;
     auto take = [&](size_t b) {
         off = round_up(off, 256);
@@ -367,11 +372,9 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
             k.M_max = std::max(k.M_max, c->cdev[ci].M);
         }
         k.total_pairs = k.pair_off.back();
-        k.cls_off = take(sizeof(int) * (k.chains.size() + k.pair_off.size()));
+        k.cls_off = take(sizeof(int) * (k.chains.size() + k.pair_off.size() + 1));  // + work counter
     }
     // FFBS grid and scratch per class
-    double total_work = 0.0;
-    for (auto &k : c->classes) total_work += double(k.total_pairs) * k.M_max * k.L * k.L * std::log2(double(k.L) + 1);
     for (auto &k : c->classes) {
         const int wpc = default_wpc(c, k.L);
         const int gpc = is_big(k.L) ? 1 : wpc * ffbs_groups_per_warp(k.L);  // wide lattices: one pair per CTA
@@ -381,8 +384,9 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
             int bps = 1;
             int rc = occupancy(c, k.L, wpc, &bps);
             if (rc) return rc;
-            const double share = total_work > 0 ? double(k.total_pairs) * k.M_max * k.L * k.L * std::log2(double(k.L) + 1) / total_work : 1.0;
-            const int cap = std::max(1, int(std::lround(double(bps) * c->num_sms * share)));
+            // every class may fill the GPU: groups take pairs from a work counter, so
+            // concurrent classes share the SMs dynamically
+            const int cap = std::max(1, bps * c->num_sms);
             grid = std::min(need, cap);
         }
         k.grid = std::max(1, grid);
@@ -543,7 +547,9 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.M_max = cl.M_max;
         fl.scratch = c->base + cl.scratch_off;
         fl.slot_elems = (long long)cl.M_max * cl.L * cl.L;
+        fl.next_pair = reinterpret_cast<unsigned *>(const_cast<int *>(fl.class_pair_off) + cl.pair_off.size());
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
+        HQMC_CUDA(c, cudaMemsetAsync(fl.next_pair, 0, sizeof(unsigned), s));
         const int wpc = default_wpc(c, cl.L);
         cudaError_t e = is_big(cl.L) ? launch_ffbs_big(cl.L, c->st, fl, cl.grid, s)
                         : f64        ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
@@ -562,7 +568,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[2], st));
     int max_L = 0;
     for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
-    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, 8, true, st);
+    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, c->slices_per_cta, true, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
     if (prof) {
         HQMC_CUDA(c, cudaEventRecord(pe[3], st));
@@ -726,6 +732,13 @@ int hqmc_set_launch(hqmc_ctx *c, int use_graph, int persistent, int warps_per_ct
     drop_graph(c);
     // the scratch size depends on the grid: lay out again at the next use, keeping the state
     if (relayout) return stash_state(c);
+    return HQMC_OK;
+}
+
+int hqmc_set_slice_launch(hqmc_ctx *c, int slices_per_cta) {
+    if (!c || slices_per_cta < 1 || slices_per_cta > 1024) return HQMC_ERR_ARG;
+    c->slices_per_cta = slices_per_cta;
+    drop_graph(c);
     return HQMC_OK;
 }
 

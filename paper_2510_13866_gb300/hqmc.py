@@ -26,6 +26,7 @@ SIGNATURES = {
     "hqmc_set_params": (_i, [_vp, _i, _d, _d, _d, _d, _d]),
     "hqmc_set_stream": (_i, [_vp, _vp]),
     "hqmc_set_launch": (_i, [_vp, _i, _i, _i]),
+    "hqmc_set_slice_launch": (_i, [_vp, _i]),
     "hqmc_set_class_launch": (_i, [_vp, _i, _i]),
     "hqmc_get_class_launch": (_i, [_vp, _i, _vp]),
     "hqmc_autotune": (_i, [_vp, _i, _vp]),
@@ -148,6 +149,9 @@ class Lattice:
         self._check(lib().hqmc_set_launch(self._ctx, int(use_graph), int(persistent), int(warps_per_cta)))
         if self.torch_memory and self._ws is not None:
             self._attach()
+
+    def set_slice_launch(self, slices_per_cta):
+        self._check(lib().hqmc_set_slice_launch(self._ctx, int(slices_per_cta)))
 
     def set_class_launch(self, L, warps_per_cta):
         self._check(lib().hqmc_set_class_launch(self._ctx, int(L), int(warps_per_cta)))
