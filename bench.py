@@ -142,6 +142,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+GRAD_WORKLOAD = ("adjoint (config 4): L=16 (N=256) t=1 U=4 beta=4 dtau=0.05 (M=80) half filling, 128 chains; "
+                 "log Z, d log Z/d v and d log Z/d t per call, BF16 checkpoints every 9 slices")
+
+
+def run_grad(args):
+    """Adjoint evaluations per second (hqmc_log_weight_grad) on the config-4 workload."""
+    import numpy as np
+    import torch
+
+    from paper_2510_13866_gb300 import Lattice
+    from paper_2510_13866_gb300.shard import chain_seeds
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    nch = args.chains if args.chains != WORK["chains"] else 128
+    p = (1.0, 4.0, 4.0, 0.05, 1.0)
+    lat = Lattice(16, chain_seeds(rank, nch), precision="fp32", device=local)
+    lat.set_params(*p)
+    lat.sweep(2)
+    for _ in range(args.warmup):
+        lat.log_weight_grad()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lat.log_weight_grad()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    L, M, ns = lat.shapes[0]
+    N = L * L
+    part = nch * 2 * ns * M
+    # forward, segment recompute and reverse pass (H and dG/dt * b): about four forward
+    # filters of 5 N log2 N + 4 N flops per particle-slice
+    flops = part * 4.0 * (5.0 * N * np.log2(N) + 4.0 * N)
+    _, _, sm_max = peaks()
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        import oracle
+
+        s, x, _, _ = lat.get_state(0)
+        orc = oracle.Chain(16, *p, 0)
+        orc.s[:] = s
+        orc.x[:] = x
+        t0 = time.perf_counter()
+        orc.grad()
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (dt * nch), "unit": "gradient evaluations/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"chain 0 in full ({dt:.2f} s), extrapolated to {nch} chains"}
+    lat.close()
+    if rank == 0:
+        line = {"metric": "gradient evaluations/s (log Z, d log Z/d v, d log Z/d t of every chain)",
+                "value": world * 1e3 / ms, "unit": "evaluations/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": GRAD_WORKLOAD, "L": L, "M": M, "chains_per_gpu": nch},
+                "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": alu_peak,
+                             "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / alu_peak, "traffic": None,
+                             "kernel": "grad_kernel<float,16>",
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+                "cpu_baseline": cpu, "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+
+
 WORKLOADS = {
     "L32": "config 2 (the headline): " + WORKLOAD,
     "ragged": ("256 ragged chains, L in {8,12,16,24,32,48}, beta in {2,4,6}, U in {2,4,8}, filling in "
@@ -151,7 +220,7 @@ WORKLOADS = {
 }
 
 
-def workload(name, rank, chains):
+def workload(name, rank, chains, beta=None):
     """(L per chain, params per chain, seeds) of a named workload on rank `rank`."""
     from paper_2510_13866_gb300.shard import chain_seeds
     from paper_2510_13866_gb300.workloads import ragged
@@ -166,7 +235,7 @@ def workload(name, rank, chains):
         return [w[0] for w in work], [w[1] for w in work], chain_seeds(rank, n)
     L = int(name[1:])
     n = chains if chains != WORK["chains"] else 16
-    return [L] * n, [(1.0, 4.0, 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
+    return [L] * n, [(1.0, 4.0, beta if beta else 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
 
 
 def kernel_source_digest():
@@ -188,8 +257,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS),
-                    help="L32 (default, the headline configuration), ragged, L64, L128")
+    ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS) + ["grad16"],
+                    help="L32 (default, the headline configuration), ragged, L64, L128; grad16 times the adjoint")
+    ap.add_argument("--beta", type=float, default=None,
+                    help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures)")
     ap.add_argument("--chains", type=int, default=WORK["chains"],
                     help="chains per GPU (default: the workload's own; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -197,6 +268,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "grad16":
+        return run_grad(args)
 
     import numpy as np
     import torch
@@ -222,7 +295,7 @@ def main():
 
     from paper_2510_13866_gb300 import Lattice
 
-    Ls, pars, seeds = workload(args.workload, rank, args.chains)
+    Ls, pars, seeds = workload(args.workload, rank, args.chains, args.beta)
     nchains = len(Ls)
 
     def make(precision):

@@ -42,6 +42,8 @@
 
 #define ORC_PI 3.14159265358979323846264338327950288
 
+int orc_num_threads(void);
+
 /* ------------------------------------------------------------------------- */
 /* Philox4x64-10 (Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", */
 /* SC'11): ten rounds of a 64x64->128 multiply S-box with a Weyl key schedule.  */
@@ -108,6 +110,15 @@ void orc_g_table(int L, double t, double dtau, double *g, double *dg)
 
 static inline int orc_wrap(int v, int L) { v %= L; return v < 0 ? v + L : v; }
 
+static inline int omp_in_parallel_safe(void)
+{
+#ifdef _OPENMP
+    return omp_in_parallel();
+#else
+    return 1;
+#endif
+}
+
 /* G(y - x) for sites x, y. */
 static inline double orc_G(const double *g, int L, int x, int y)
 {
@@ -122,10 +133,13 @@ static inline double orc_dG(const double *g, const double *dg, int L, int x, int
     return dg[dx] * g[dy] + g[dx] * dg[dy];
 }
 
-/* out(y) = sum_x K(y - x) in(x): direct periodic convolution, O(N^2). */
+/* out(y) = sum_x K(y - x) in(x): direct periodic convolution, O(N^2).  Large lattices
+ * split the output sites over threads when no outer loop is parallel (each out(y) is
+ * still one sequential sum, so the result does not depend on the thread count). */
 static void orc_conv(int L, const double *g, const double *in, double *out)
 {
     int N = L * L;
+#pragma omp parallel for schedule(static) if (N >= 1024 && !omp_in_parallel_safe())
     for (int y = 0; y < N; ++y) {
         double acc = 0.0;
         for (int x = 0; x < N; ++x) acc += orc_G(g, L, x, y) * in[x];
@@ -136,6 +150,7 @@ static void orc_conv(int L, const double *g, const double *in, double *out)
 static void orc_conv_dG(int L, const double *g, const double *dg, const double *in, double *out)
 {
     int N = L * L;
+#pragma omp parallel for schedule(static) if (N >= 1024 && !omp_in_parallel_safe())
     for (int y = 0; y < N; ++y) {
         double acc = 0.0;
         for (int x = 0; x < N; ++x) acc += orc_dG(g, dg, L, x, y) * in[x];
@@ -277,7 +292,9 @@ int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t 
     }
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
     int total = 2 * nwl;
-#pragma omp parallel for schedule(dynamic, 1)
+    /* worldlines in parallel when there are enough of them; otherwise the convolution
+     * itself runs in parallel over output sites */
+#pragma omp parallel for schedule(dynamic, 1) if (total >= 2 * orc_num_threads())
     for (int k = 0; k < total; ++k) {
         int sg = k / nwl, p = k % nwl;
         uint64_t wl = (uint64_t)sg * Nsig + p;

@@ -95,7 +95,12 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
         }
     };
 
-    for (long long q = gid; q < gk.total_pairs; q += ngroups) {
+    (void)ngroups;
+    for (;;) {
+        unsigned qn = 0;
+        if (gl == 0) qn = atomicAdd(gk.next_pair, 1u);
+        const long long q = (long long)__shfl_sync(gmask, qn, 0, GW);
+        if (q >= gk.total_pairs) break;
         int lo = 0, hi = gk.nclass - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -262,7 +267,15 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
                 b[r].y = (bC ? (gl == ax1 && r == ay1) : (gl == ay1 && r == ax1)) ? T(1) : T(0);
             }
         }
-        double dt0 = 0.0, dt1 = 0.0;
+        // d log Z / dt: per-slice ratios in the context precision, compensated (Kahan) sums
+        // (no FP64 instruction per slice in the FP32 context)
+        T dts0 = T(0), dtc0 = T(0), dts1 = T(0), dtc1 = T(0);
+        auto kahan = [](T &sum, T &comp, T v) {
+            const T y = v - comp;
+            const T t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        };
         const int nseg = (M + K - 1) / K;
         for (int s = nseg - 1; s >= 0; --s) {
             const int lb = s * K, le = min(M, lb + K);
@@ -325,8 +338,8 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
                 if (!(z0 > T(0)) || (has1 && !(z1 > T(0)))) {
                     if (gl == 0) atomicOr(st.status, kStatusNonPositive);
                 }
-                dt0 += double(zd0) / double(z0);
-                dt1 += double(zd1) / double(z1);
+                kahan(dts0, dtc0, zd0 / z0);
+                kahan(dts1, dtc1, zd1 / z1);
                 if (dvp && active) {
                     const T iz0 = T(1) / z0, iz1 = has1 ? T(1) / z1 : T(0);
                     T *dvl = dvp + (long long)l * N;
@@ -347,7 +360,7 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
                 for (int r = 0; r < L; ++r) b[r] = vmul(b[r], sc);
             }
         }
-        if (gl == 0) atomicAdd(&gk.dt[c], dt0 + (has1 ? dt1 : 0.0));
+        if (gl == 0) atomicAdd(&gk.dt[c], double(dts0) + (has1 ? double(dts1) : 0.0));
         __syncwarp(gmask);
     }
     (void)CH;

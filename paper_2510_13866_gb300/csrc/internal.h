@@ -107,6 +107,7 @@ struct GradLaunch {
     void *dv;                  // d log Z / d v, same layout (nullable), zeroed by the caller
     double *logz;              // [chain], zeroed by the caller
     double *dt;                // [chain], zeroed by the caller
+    unsigned *next_pair;       // work counter, zeroed by the caller
 };
 
 // Launchers (defined in the per-precision translation units).

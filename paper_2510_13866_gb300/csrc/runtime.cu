@@ -1046,7 +1046,8 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
     for (const LClass &cl : c->classes)
         if (is_big(cl.L)) return fail(c, HQMC_ERR_UNSUPPORTED, "the adjoint covers L <= 32");
     std::vector<Plan> plans(c->classes.size());
-    size_t off = round_up(size_t(c->nchains) * 16, 256);  // logz, dt per chain
+    const size_t head = size_t(c->nchains) * 16 + c->classes.size() * 4;  // logz, dt per chain; counters
+    size_t off = round_up(head, 256);
     for (size_t k = 0; k < c->classes.size(); ++k) {
         const LClass &cl = c->classes[k];
         Plan &p = plans[k];
@@ -1084,7 +1085,8 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
     cudaStream_t st = c->stream;
     double *d_logz = reinterpret_cast<double *>(c->grad_mem);
     double *d_dt = d_logz + c->nchains;
-    HQMC_CUDA(c, cudaMemsetAsync(d_logz, 0, size_t(c->nchains) * 16, st));
+    unsigned *d_next = reinterpret_cast<unsigned *>(d_dt + c->nchains);
+    HQMC_CUDA(c, cudaMemsetAsync(d_logz, 0, head, st));
     if (dlogZ_dv) HQMC_CUDA(c, cudaMemsetAsync(dlogZ_dv, 0, size_t(c->total_v) * tsz, st));
     for (size_t k = 0; k < c->classes.size(); ++k) {
         const LClass &cl = c->classes[k];
@@ -1105,6 +1107,7 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
         gk.dv = dlogZ_dv;
         gk.logz = d_logz;
         gk.dt = d_dt;
+        gk.next_pair = d_next + k;
         cudaError_t e = f64 ? launch_grad_f64(cl.L, c->st, gk, p.grid, st) : launch_grad_f32(cl.L, c->st, gk, p.grid, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "grad launch");
     }

@@ -127,3 +127,26 @@ def test_wide_measure_matches_oracle_on_gpu_paths(L):
     assert np.allclose(m["Sk"], mo["Sk"] / (4 * M), rtol=1e-4, atol=1e-5)
     assert np.allclose(m["Cr"], mo["Cr"] / (4 * M), rtol=1e-4, atol=1e-5)
     lat.close()
+
+
+@pytest.mark.parametrize("L,nwl", [(64, 1), (128, 1)])
+def test_wide_full_size_sampled(L, nwl):
+    """Large-lattice configuration at full size: L = 64 or 128, t=1, U=4, beta=8,
+    dtau=0.05 (M=160), half filling, 16 chains, one sweep in the benchmark's launch
+    configuration; the oracle recomputes the first worldline of each spin of chain 0."""
+    from paper_2510_13866_gb300 import Lattice
+
+    params = (1.0, 4.0, 8.0, 0.05, 1.0)
+    lat = Lattice(L, list(range(16)), precision="fp32")
+    lat.set_params(*params)
+    logw = lat.sweep(1, logw=True)
+    for c in range(16):
+        assert np.all(np.isfinite(logw[c]))
+    orc = oracle.Chain(L, *params, 0)
+    ref = orc.sweep(want_margin=True, nwl_limit=nwl)
+    s, x, a, _ = lat.get_state(0)
+    assert a == ref["anchor"]
+    assert rel_err(logw[0][:, :nwl], ref["logw"][:, :nwl]).max() <= 1e-5
+    _, _, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 1e-5, nwl=nwl)
+    assert not bad, bad[:3]
+    lat.close()
