@@ -29,10 +29,15 @@ namespace hqmc {
 
 template <int L>
 struct BigGeo {
-    static constexpr int S = (L > 64) ? 2 : 1;          // threads per lattice line
+    // threads per lattice line: two at L = 48 (three full warps per pair, 119 registers,
+    // five CTAs per SM) and L = 128 (the line does not fit one thread); one at L = 64,
+    // where the pair split over 128 threads measured 26% slower than 64 threads
+    static constexpr int S = (L == 48 || L > 64) ? 2 : 1;
     static constexpr int E = L / S;                      // line elements per thread
     static constexpr int NT = ((L * S + 31) / 32) * 32;  // threads per CTA (one pair)
     static constexpr int NW = NT / 32;
+    // resident CTAs per SM the register budget is sized for
+    static constexpr int MINB = (L == 48) ? 5 : 1;
     static constexpr int n = L / 2;                      // half-length complex FFT size
     static constexpr int m = n / S;                      // per-thread FFT size
     static constexpr int LP = (S == 2) ? L + 4 : L + 2;  // transpose pitch (elements)
@@ -142,7 +147,7 @@ __device__ __forceinline__ void big_conv(float2 (&v)[BigGeo<L>::E], const float2
 }
 
 template <int L>
-__global__ void __launch_bounds__(BigGeo<L>::NT, 1) ffbs_big_kernel(DevState st, FfbsLaunch fl) {
+__global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kernel(DevState st, FfbsLaunch fl) {
     using B = BigGeo<L>;
     using V = float2;
     using T = float;
