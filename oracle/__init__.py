@@ -43,6 +43,13 @@ def lib():
         L.orc_chain_grad.argtypes = [i, i, i, d, d, d, vp, vp, vp, vp, vp]
         L.orc_chain_grad.restype = d
         L.orc_measure.argtypes = [i, i, vp, vp, vp, vp]
+        L.orc_normal.argtypes = [d, d]
+        L.orc_normal.restype = d
+        L.orc_gauss_coupling.argtypes = [d, d]
+        L.orc_gauss_coupling.restype = d
+        L.orc_init_sigma.argtypes = [i, i, u64, vp]
+        L.orc_sweep_gauss.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i]
+        L.orc_sweep_gauss.restype = i
         L.orc_num_threads.restype = i
         _lib = L
     return _lib
@@ -94,8 +101,17 @@ def initial_site(L, sigma, p):
     return lib().orc_initial_site(L, sigma, p)
 
 
+def normal(u1, u2):
+    return lib().orc_normal(u1, u2)
+
+
+def gauss_coupling(U, dtau):
+    return lib().orc_gauss_coupling(U, dtau)
+
+
 class Chain:
-    """One Markov chain's state in the oracle."""
+    """One Markov chain's state in the oracle.  U >= 0: Hirsch field s (int8 +-1);
+    U < 0: continuous Gaussian field sigma (float64)."""
 
     def __init__(self, L, t, U, beta, dtau, filling, seed):
         self.L, self.t, self.U, self.beta, self.dtau = L, t, U, beta, dtau
@@ -104,9 +120,14 @@ class Chain:
         self.Nsig = n_sigma(L, filling)
         self.seed = seed
         self.sweep_count = 0
+        self.gauss = U < 0
         self.s = np.zeros((self.M, self.N), dtype=np.int8)
         self.x = np.zeros((2, self.Nsig, self.M), dtype=np.int32)
         lib().orc_init_state(L, self.M, self.Nsig, seed, _p(self.s), _p(self.x))
+        self.sigma = None
+        if self.gauss:
+            self.sigma = np.zeros((self.M, self.N))
+            lib().orc_init_sigma(L, self.M, seed, _p(self.sigma))
 
     @property
     def lam(self):
@@ -120,9 +141,14 @@ class Chain:
         margin = np.full((2, Ns, M), np.nan) if want_margin else None
         links = np.full((2, Ns), np.nan)
         anchor = C.c_int(-1)
-        lib().orc_sweep(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
-                        _p(self.s), _p(self.x), _p(logw), _p(hist), _p(margin), _p(links),
-                        C.byref(anchor), nwl_limit)
+        if self.gauss:
+            lib().orc_sweep_gauss(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
+                                  _p(self.sigma), _p(self.x), _p(logw), _p(hist), _p(margin), _p(links),
+                                  C.byref(anchor), nwl_limit)
+        else:
+            lib().orc_sweep(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
+                            _p(self.s), _p(self.x), _p(logw), _p(hist), _p(margin), _p(links),
+                            C.byref(anchor), nwl_limit)
         self.sweep_count += 1
         out = dict(logw=logw, hist=hist, anchor=anchor.value, links=links)
         if want_margin:

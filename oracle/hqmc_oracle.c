@@ -272,25 +272,16 @@ void orc_backward(int L, int M, const double *g, const double *f_store, int a,
  *   nwl_limit: if >= 0, only the first nwl_limit worldlines of each spin are
  *   resampled (a bounded sample for timing); the Gibbs step is then skipped.
  * Worldlines are independent given s, so they are processed in parallel. */
-int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
-              int8_t *s, int32_t *xpath, double *logw, int32_t *hist, double *margin,
-              double *links, int *anchor, int nwl_limit)
+/* FFBS of every worldline (the first nwl of each spin) given the slice potentials
+ * W [2][M][N] (spin-major): anchor, filter, backward draw, link sums. */
+static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
+                        uint64_t seed, uint64_t sweep, int32_t *xpath, double *logw, double *margin,
+                        double *links, int *anchor, int nwl)
 {
     int N = L * L;
-    double lam = orc_lambda(U, dtau);
-    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
-    orc_g_table(L, t, dtau, g, dg);
     int a = (int)floor(orc_uniform(seed, sweep, 2, 0, 0) * M);
     if (a >= M) a = M - 1;
     if (anchor) *anchor = a;
-    double *W = malloc((size_t)2 * M * N * sizeof(double));
-    for (int sg = 0; sg < 2; ++sg) {
-        double sigma = sg == 0 ? 1.0 : -1.0;
-        for (int l = 0; l < M; ++l)
-            for (int x = 0; x < N; ++x)
-                W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
-    }
-    int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
     int total = 2 * nwl;
     /* worldlines in parallel when there are enough of them; otherwise the convolution
      * itself runs in parallel over output sites */
@@ -314,19 +305,112 @@ int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t 
         }
         free(fst);
     }
+    return a;
+}
+
+/* Occupancy histogram [2][M][N] of the current worldlines. */
+static void orc_histogram(int L, int M, int Nsig, const int32_t *xpath, int32_t *n)
+{
+    int N = L * L;
+    memset(n, 0, (size_t)2 * M * N * sizeof(int32_t));
+    for (int sg = 0; sg < 2; ++sg)
+        for (int p = 0; p < Nsig; ++p)
+            for (int l = 0; l < M; ++l)
+                n[((size_t)sg * M + l) * N + xpath[((size_t)sg * Nsig + p) * M + l]] += 1;
+}
+
+int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
+              int8_t *s, int32_t *xpath, double *logw, int32_t *hist, double *margin,
+              double *links, int *anchor, int nwl_limit)
+{
+    int N = L * L;
+    double lam = orc_lambda(U, dtau);
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    double *W = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg) {
+        double sigma = sg == 0 ? 1.0 : -1.0;
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x)
+                W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
+    }
+    int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
-        memset(n, 0, (size_t)2 * M * N * sizeof(int32_t));
-        for (int sg = 0; sg < 2; ++sg)
-            for (int p = 0; p < Nsig; ++p)
-                for (int l = 0; l < M; ++l)
-                    n[((size_t)sg * M + l) * N + xpath[((size_t)sg * Nsig + p) * M + l]] += 1;
+        orc_histogram(L, M, Nsig, xpath, n);
         for (int l = 0; l < M; ++l)
             for (int x = 0; x < N; ++x) {
                 int m = n[(size_t)l * N + x] - n[((size_t)M + l) * N + x];
                 double pplus = 1.0 / (1.0 + exp(-2.0 * lam * m));
                 double u = orc_uniform(seed, sweep, 1, (uint64_t)l, (uint64_t)x);
                 s[(size_t)l * N + x] = (u < pplus) ? 1 : -1;
+            }
+        if (!hist) free(n);
+    }
+    free(g); free(dg); free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Attractive U < 0: continuous Gaussian field (Sec. 3.5.5, Eq. gaussHS,      */
+/* Eq. gaussCond).  Reading: a = sqrt(|U| dtau) and the shift n - 1/2 of the   */
+/* main text (the appendix's sqrt(|U| dtau / 2)(n - 1) does not reproduce     */
+/* exp(|U| dtau n_up n_dn)).  Every worldline, of either spin, sees            */
+/* W_l(x) = exp(a sigma_{x,l}); the factor exp(-a sigma / 2) and the Gaussian  */
+/* belong to the field's own weight.                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Standard normal from two uniforms in [0,1) by the Box-Muller transform (Box and
+ * Muller, 1958): z = sqrt(-2 ln(1 - u1)) cos(2 pi u2). */
+double orc_normal(double u1, double u2)
+{
+    return sqrt(-2.0 * log(1.0 - u1)) * cos(2.0 * ORC_PI * u2);
+}
+
+/* a = sqrt(|U| dtau). */
+double orc_gauss_coupling(double U, double dtau)
+{
+    return sqrt(fabs(U) * dtau);
+}
+
+/* Initial field: sigma[l][x] standard normal from phase 3 (sweep 2^64-1), j = 2x, 2x+1. */
+void orc_init_sigma(int L, int M, uint64_t seed, double *sigma)
+{
+    int N = L * L;
+    for (int l = 0; l < M; ++l)
+        for (int x = 0; x < N; ++x)
+            sigma[(size_t)l * N + x] = orc_normal(orc_uniform(seed, UINT64_MAX, 3, (uint64_t)l, 2 * (uint64_t)x),
+                                                  orc_uniform(seed, UINT64_MAX, 3, (uint64_t)l, 2 * (uint64_t)x + 1));
+}
+
+/* One sweep with the Gaussian field: FFBS as in orc_sweep with W = exp(a sigma) for both
+ * spins, then sigma_{x,l} ~ N(a (n_up + n_dn - 1/2), 1), drawn from phase 1 with
+ * j = 2x, 2x+1. */
+int orc_sweep_gauss(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
+                    double *sigma, int32_t *xpath, double *logw, int32_t *hist, double *margin,
+                    double *links, int *anchor, int nwl_limit)
+{
+    int N = L * L;
+    double a = orc_gauss_coupling(U, dtau);
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    double *W = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg)
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x)
+                W[((size_t)sg * M + l) * N + x] = exp(a * sigma[(size_t)l * N + x]);
+    int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl);
+    if (nwl_limit < 0 || nwl_limit >= Nsig) {
+        int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
+        orc_histogram(L, M, Nsig, xpath, n);
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x) {
+                int nt = n[(size_t)l * N + x] + n[((size_t)M + l) * N + x];
+                double u1 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x);
+                double u2 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x + 1);
+                sigma[(size_t)l * N + x] = a * (nt - 0.5) + orc_normal(u1, u2);
             }
         if (!hist) free(n);
     }

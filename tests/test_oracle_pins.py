@@ -278,14 +278,19 @@ def test_gibbs_conditional_frequencies(orc):
 def two_particle_exact(L, t, U, dtau, M):
     """Exact Trotterised Z, double occupancy per site and kinetic energy per site for
     one up and one down worldline (no same-spin exchange exists, so P = identity is exact).
-    Summing the Hirsch field gives prod_x cosh(lambda m_x) = exp(dtau U) if apart, 1 if together."""
+    U > 0: summing the Hirsch field gives prod_x cosh(lambda m_x) = exp(dtau U) if apart,
+    1 if together.  U < 0: integrating the Gaussian field gives prod_x exp(a^2 (n_x - 1/2)^2 / 2),
+    a^2 = |U| dtau, which is exp(|U| dtau) more when together than apart."""
     N = L * L
 
     def logZ_and_D(tt):
         G = sla.expm(tt * dtau * lattice_adjacency(L))
         GG = np.kron(G, G)  # index x_up * N + x_dn
         same = np.array([1.0 if (i // N) == (i % N) else 0.0 for i in range(N * N)])
-        V = np.where(same > 0, 1.0, math.exp(dtau * U))
+        if U >= 0:
+            V = np.where(same > 0, 1.0, math.exp(dtau * U))
+        else:
+            V = np.where(same > 0, math.exp(-dtau * U), 1.0)
         T = GG * V[None, :]
         TM = np.linalg.matrix_power(T, M)
         Z = np.trace(TM)
@@ -326,6 +331,58 @@ def test_sweep_two_particle_exact(orc):
     em, ee = _batch_stats(Es)
     assert abs(dm - D_ex) < 4.5 * de + 1e-4, (dm, de, D_ex)
     assert abs(em - E_ex) < 4.5 * ee + 1e-4, (em, ee, E_ex)
+
+
+def test_sweep_two_particle_exact_attractive(orc):
+    """U < 0 with the Gaussian field: FFBS + Gaussian Gibbs against the exact two-particle
+    double occupancy and kinetic energy (the field integrated out in closed form)."""
+    L, U, dtau, beta = 3, -4.0, 0.25, 1.0
+    M = 4
+    filling = 2.0 / (L * L)
+    D_ex, E_ex = two_particle_exact(L, 1.0, U, dtau, M)
+    ch = orc.Chain(L=L, t=1.0, U=U, beta=beta, dtau=dtau, filling=filling, seed=6)
+    Ds, Es = [], []
+    for k in range(24000):
+        out = ch.sweep()
+        if k < 500:
+            continue
+        m = orc.measure(L, M, out["hist"], want_fields=False)
+        Ds.append(m["d"] / (M * L * L))
+        Es.append(-(1.0 / beta) * out["links"].sum() / (L * L))
+    dm, de = _batch_stats(Ds)
+    em, ee = _batch_stats(Es)
+    assert abs(dm - D_ex) < 4.5 * de + 1e-4, (dm, de, D_ex)
+    assert abs(em - E_ex) < 4.5 * ee + 1e-4, (em, ee, E_ex)
+
+
+def test_box_muller_normal(orc):
+    """Box-Muller output of independent uniforms is standard normal (Kolmogorov-Smirnov)."""
+    from scipy import stats
+
+    rng = np.random.default_rng(11)
+    u = rng.random((20000, 2))
+    z = np.array([orc.normal(a, b) for a, b in u])
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert orc.normal(0.0, 0.0) == 0.0  # 1 - u1 = 1: radius zero
+
+
+def test_gauss_conditional_moments(orc):
+    """Gaussian Gibbs: sigma | paths ~ N(a (n - 1/2), 1) (Eq. gaussCond), a = sqrt(|U| dtau)."""
+    ch = orc.Chain(L=4, t=1.0, U=-6.0, beta=0.5, dtau=0.1, filling=1.0, seed=3)
+    a = math.sqrt(6.0 * 0.1)
+    assert abs(orc.gauss_coupling(-6.0, 0.1) - a) < 1e-15
+    buckets = {}
+    for _ in range(400):
+        out = ch.sweep()
+        n = out["hist"][0] + out["hist"][1]
+        for nv, sv in zip(n.ravel(), ch.sigma.ravel()):
+            buckets.setdefault(int(nv), []).append(sv - a * (nv - 0.5))
+    for nv, r in buckets.items():
+        if len(r) < 500:
+            continue
+        r = np.asarray(r)
+        assert abs(r.mean()) < 5 / math.sqrt(len(r)), (nv, r.mean())
+        assert abs(r.var() - 1.0) < 5 * math.sqrt(2.0 / len(r)), (nv, r.var())
 
 
 def test_sweep_u0_kinetic_energy(orc):
