@@ -88,12 +88,18 @@ typedef struct {
 int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t *seeds,
                       int precision, int device);
 
-/* Model parameters of chain `chain` (-1 = all chains): hopping t >= 0, U >= 0,
+/* Model parameters of chain `chain` (-1 = all chains): hopping t >= 0, U (finite),
  * inverse temperature beta and slice dtau with beta/dtau an integer M (within 1e-9),
  * filling with filling*N/2 a positive integer Nsig (worldlines per spin, 2 Nsig <= 2N).
- * U < 0 (the Gaussian transformation of Sec. 3.5.5) is rejected.
- * Before the first sweep any parameter may change; afterwards only t and U may change
- * (M and Nsig fix the state's shape), else HQMC_ERR_STATE.  Errors: HQMC_ERR_ARG. */
+ * U >= 0 uses the discrete Hirsch field s = +-1 (Sec. 3.5.4): W = exp(sigma lambda s),
+ * cosh lambda = exp(dtau U / 2).  U < 0 uses the continuous Gaussian field of Sec. 3.5.5
+ * (Eq. gaussHS): W = exp(a sigma_{x,l}) for both spins, a = sqrt(|U| dtau), and the Gibbs
+ * step draws sigma ~ N(a (n_up + n_dn - 1/2), 1) (Eq. gaussCond; reading: the main text's
+ * a and shift, which reproduce exp(|U| dtau n_up n_dn); the appendix's sqrt(|U| dtau / 2)
+ * and n - 1 do not).  Gaussian draws: Box-Muller from the uniforms of j = 2x and 2x+1.
+ * Before the first sweep any parameter may change; afterwards only t, U and (beta,
+ * dtau) at fixed M may change, and U keeps its sign (M, Nsig and the field type fix the
+ * state), else HQMC_ERR_STATE.  Errors: HQMC_ERR_ARG, HQMC_ERR_UNSUPPORTED. */
 int hqmc_set_params(hqmc_ctx *ctx, int chain, double t, double U, double beta, double dtau,
                     double filling);
 
@@ -192,10 +198,17 @@ int hqmc_log_weight_grad(hqmc_ctx *ctx, const void *v, double *logZ, void *dlogZ
 int hqmc_chain_shape(hqmc_ctx *ctx, int chain, int *L, int *M, int *Nsig);
 
 /* Copy chain c's state to host buffers (each nullable):
- *   s [M][N] int8 (+1/-1), x [2][Nsig][M] int32 sites, anchor = last anchor slice
+ *   s [M][N] int8 (+1/-1; zeros for a U < 0 chain, whose field is read with
+ *   hqmc_get_sigma), x [2][Nsig][M] int32 sites, anchor = last anchor slice
  *   (-1 before the first sweep), sweeps = sweeps done.  Errors: HQMC_ERR_STATE, _CUDA. */
 int hqmc_get_state(hqmc_ctx *ctx, int chain, int8_t *s, int32_t *x, int *anchor,
                    uint64_t *sweeps);
+
+/* Gaussian field sigma [M][N] (doubles) of a U < 0 chain, to or from host memory; setting
+ * it recomputes the chain's slice potentials.  Errors: HQMC_ERR_ARG (null, a U >= 0
+ * chain, non-finite values), HQMC_ERR_STATE, HQMC_ERR_CUDA. */
+int hqmc_get_sigma(hqmc_ctx *ctx, int chain, double *sigma);
+int hqmc_set_sigma(hqmc_ctx *ctx, int chain, const double *sigma);
 
 /* Overwrite chain c's field and worldlines (layouts as in hqmc_get_state; sites must be
  * in [0, N), s in {-1, +1}); sweeps (if non-NULL) sets the sweep counter of the whole

@@ -73,6 +73,32 @@ __device__ __forceinline__ const float *tab_g<float>(const ChainTab &tb) { retur
 template <>
 __device__ __forceinline__ const double *tab_g<double>(const ChainTab &tb) { return tb.g_d; }
 
+// Slice potential of a Gaussian-field chain (U < 0): W_l(ix, iy) from the row array
+// (lines = y, iy-major) or the column array (lines = x, ix-major), context precision.
+template <typename T>
+__device__ __forceinline__ const T *gauss_line(const DevState &st, const ChainDev &cd, bool cols, int l, int line) {
+    return static_cast<const T *>(st.gw) + 2 * cd.g_off + (cols ? (long long)cd.M * cd.N : 0) +
+           (long long)l * cd.N + (long long)line * cd.L;
+}
+
+// v[r] *= W_l(line, r) (s0, s1): one line of a Gaussian-field chain's slice potential
+template <typename T, int L, typename V>
+__device__ __forceinline__ void mul_gauss_line(V (&v)[L], const T *w, T s0, T s1) {
+    if constexpr (sizeof(T) == 4 && L % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < L / 4; ++j) {
+            const float4 q = reinterpret_cast<const float4 *>(w)[j];
+            v[4 * j] = vmul(v[4 * j], V{q.x * s0, q.x * s1});
+            v[4 * j + 1] = vmul(v[4 * j + 1], V{q.y * s0, q.y * s1});
+            v[4 * j + 2] = vmul(v[4 * j + 2], V{q.z * s0, q.z * s1});
+            v[4 * j + 3] = vmul(v[4 * j + 3], V{q.w * s0, q.w * s1});
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < L; ++r) v[r] = vmul(v[r], V{w[r] * s0, w[r] * s1});
+    }
+}
+
 // pick element r of a register array with a runtime index (no local-memory spill)
 template <int L, typename V>
 __device__ __forceinline__ V reg_select(const V (&v)[L], int r) {
@@ -184,12 +210,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         V v[L];
         {
             // f_a = W_a(x_a) delta_{x_a}, layout R: lane = iy, register = ix
-            const uint32_t w = active ? srow[((long long)a * L + gl) * cd.wpl] : 0u;
+            T wv0, wv1;
+            if (cd.gauss) {
+                wv0 = gauss_line<T>(st, cd, false, a, ay0)[ax0];
+                wv1 = gauss_line<T>(st, cd, false, a, ay1)[ax1];
+            } else {
+                wv0 = ((srow[((long long)a * L + ay0) * cd.wpl + (ax0 >> 5)] >> (ax0 & 31)) & 1u) ? wp : wm;
+                wv1 = ((srow[((long long)a * L + ay1) * cd.wpl + (ax1 >> 5)] >> (ax1 & 31)) & 1u) ? wp : wm;
+            }
 #pragma unroll
             for (int r = 0; r < L; ++r) {
-                const T wv = ((w >> r) & 1u) ? wp : wm;
-                v[r].x = (gl == ay0 && r == ax0) ? wv : T(0);
-                v[r].y = (gl == ay1 && r == ax1) ? wv : T(0);
+                v[r].x = (gl == ay0 && r == ax0) ? wv0 : T(0);
+                v[r].y = (gl == ay1 && r == ax1) ? wv1 : T(0);
             }
         }
         int esum0 = 0, esum1 = 0;
@@ -255,11 +287,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 esum1 += e1;
                 const T sc0 = fbits<T>::pow2(-e0), sc1 = fbits<T>::pow2(-e1);
                 const V A = {wp * sc0, wp * sc1}, B = {wm * sc0, wm * sc1};
-                // the new layout is C (lane = ix) when i is even: bits by columns
-                const uint32_t *wsrc = (i & 1) ? srow : scol;
-                const uint32_t w = active ? wsrc[((long long)l1 * L + gl) * cd.wpl] : 0u;
+                // the new layout is C (lane = ix) when i is even: the field by columns
+                if (cd.gauss) {
+                    if (active) mul_gauss_line<T, L>(v, gauss_line<T>(st, cd, (i & 1) == 0, l1, gl), sc0, sc1);
+                } else {
+                    const uint32_t *wsrc = (i & 1) ? srow : scol;
+                    const uint32_t w = active ? wsrc[((long long)l1 * L + gl) * cd.wpl] : 0u;
 #pragma unroll
-                for (int r = 0; r < L; ++r) v[r] = vmul(v[r], ((w >> r) & 1u) ? A : B);
+                    for (int r = 0; r < L; ++r) v[r] = vmul(v[r], ((w >> r) & 1u) ? A : B);
+                }
             } else {
                 // alpha_M(x_a): final layout is C if M is odd
                 const bool finC = (M & 1) != 0;

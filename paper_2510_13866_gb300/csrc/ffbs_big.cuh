@@ -243,14 +243,19 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         // ---- forward filter ----
         V v[E];
         {
-            uint32_t wb[(L + 31) / 32] = {};
-            if (active) load_bits(srow, a, p, wb, wpl);
+            T wv0, wv1;
+            if (cd.gauss) {
+                wv0 = gauss_line<T>(st, cd, false, a, ay0)[ax0];
+                wv1 = gauss_line<T>(st, cd, false, a, ay1)[ax1];
+            } else {
+                wv0 = ((srow[((long long)a * L + ay0) * wpl + (ax0 >> 5)] >> (ax0 & 31)) & 1u) ? wp : wm;
+                wv1 = ((srow[((long long)a * L + ay1) * wpl + (ax1 >> 5)] >> (ax1 & 31)) & 1u) ? wp : wm;
+            }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int pos = big_pos<L>(e, s);
-                const T wv = ((wb[big_word<L>(e)] >> big_bit<L>(e, s)) & 1u) ? wp : wm;
-                v[e].x = (active && p == ay0 && pos == ax0) ? wv : T(0);
-                v[e].y = (active && p == ay1 && pos == ax1) ? wv : T(0);
+                v[e].x = (active && p == ay0 && pos == ax0) ? wv0 : T(0);
+                v[e].y = (active && p == ay1 && pos == ax1) ? wv1 : T(0);
             }
         }
         int esum0 = 0, esum1 = 0;
@@ -301,7 +306,15 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
                 esum1 += e1;
                 const T sc0 = fbits<T>::pow2(-e0), sc1 = fbits<T>::pow2(-e1);
                 const V A = {wp * sc0, wp * sc1}, Bv = {wm * sc0, wm * sc1};
-                if (active) {
+                if (active && cd.gauss) {
+                    const T *w = gauss_line<T>(st, cd, (i & 1) == 0, l1, p);
+#pragma unroll
+                    for (int j = 0; j < E / 2; ++j) {
+                        const float2 q = *reinterpret_cast<const float2 *>(w + big_pos<L>(2 * j, s));
+                        v[2 * j] = vmul(v[2 * j], V{q.x * sc0, q.x * sc1});
+                        v[2 * j + 1] = vmul(v[2 * j + 1], V{q.y * sc0, q.y * sc1});
+                    }
+                } else if (active) {
                     uint32_t wb[(L + 31) / 32];
                     load_bits((i & 1) ? srow : scol, l1, p, wb, wpl);
 #pragma unroll

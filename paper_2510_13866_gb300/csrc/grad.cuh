@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
                     const T w = exp_t<T>(vl[site(l, r)]);
                     v[r] = vmul(v[r], V{w * s0, w * s1});
                 }
+            } else if (cd.gauss) {
+                mul_gauss_line<T, L>(v, gauss_line<T>(st, cd, (l & 1) != 0, l, gl), s0, s1);
             } else {
                 const uint32_t *wsrc = (l & 1) ? scol : srow;
                 const uint32_t w = wsrc[((long long)l * L + gl) * cd.wpl];

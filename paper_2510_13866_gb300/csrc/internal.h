@@ -40,6 +40,10 @@ struct ChainDev {
     double w_plus[2]; // W for s = +1, spin up / down: e^{+lambda}, e^{-lambda}
     double w_minus[2];
     double t, beta;
+    int gauss;          // 1: U < 0, continuous Gaussian field sigma, W = exp(gcoup sigma), both spins
+    double gcoup;       // sqrt(|U| dtau)
+    long long g_off;    // element offset of sigma [M][N] (doubles); W at 2 g_off: rows [M][L][L]
+                        // (iy-major) then columns [M][L][L] (ix-major), context precision
     long long s_off;    // word offset of the field: rows [M][L][wpl] then cols [M][L][wpl]
     long long x_off;    // int16 offset of worldlines [2][Nsig][M]
     long long h_off;    // int32 offset of the occupancy histogram [2][M][N]
@@ -74,6 +78,9 @@ struct DevState {
     unsigned long long *dens;  // per chain N: sum of n_up + n_dn per site (kept for diagnostics)
     unsigned long long *sweep; // device sweep counter
     unsigned *status;    // error bits
+    double *gsig;        // Gaussian fields sigma (U < 0 chains)
+    void *gw;            // their slice potentials W = exp(a sigma), rows then columns
+    int gw_f64;          // W stored as double (FP64 context) or float
 };
 
 enum : unsigned { kStatusDegenerate = 1u, kStatusNonPositive = 2u, kStatusTimeout = 4u };
@@ -124,6 +131,7 @@ cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, 
 cudaError_t configure_slice();
 void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
+cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStream_t stream);
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
                            double *sk_out, long long total_N, cudaStream_t stream);
 

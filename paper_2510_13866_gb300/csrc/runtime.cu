@@ -108,6 +108,7 @@ struct hqmc_ctx {
     bool pending_restore = false;
     std::vector<uint32_t> keep_bits;
     std::vector<int16_t> keep_x;
+    std::vector<double> keep_sig;
     unsigned long long keep_sweep = 0;
     bool keep_started = false;
 
@@ -238,7 +239,7 @@ namespace {
 int check_params(hqmc_ctx *c, int L, double t, double U, double beta, double dtau, double filling, int *M,
                  int *Nsig) {
     if (!(t >= 0.0) || !std::isfinite(t)) return fail(c, HQMC_ERR_ARG, "t must be finite and >= 0");
-    if (!(U >= 0.0) || !std::isfinite(U)) return fail(c, HQMC_ERR_ARG, "U must be finite and >= 0 (U < 0 needs the Gaussian field)");
+    if (!std::isfinite(U)) return fail(c, HQMC_ERR_ARG, "U must be finite");
     if (!(beta > 0.0) || !(dtau > 0.0) || !std::isfinite(beta) || !std::isfinite(dtau))
         return fail(c, HQMC_ERR_ARG, "beta and dtau must be positive");
     const double mr = beta / dtau;
@@ -317,7 +318,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     };
     const size_t o_chains = take(sizeof(ChainDev) * nc);
     const size_t o_tabs = take(sizeof(ChainTab) * nc);
-    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0;
+    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0, gb = 0;
     for (int i = 0; i < nc; ++i) {
         const HostChain &h = c->ch[i];
         ChainDev &d = c->cdev[i];
@@ -335,6 +336,10 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         d.w_minus[1] = std::exp(d.lam);
         d.t = h.t;
         d.beta = h.beta;
+        d.gauss = h.U < 0.0 ? 1 : 0;
+        d.gcoup = std::sqrt(std::fabs(h.U) * h.dtau);
+        d.g_off = gb;
+        if (d.gauss) gb += ((long long)h.M * h.N + 3) / 4 * 4;  // 16-byte aligned W lines
         d.s_off = sb;
         sb += 2LL * h.M * h.L * d.wpl;
         d.x_off = xb;
@@ -361,6 +366,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     const size_t o_dn = take(size_t(mb) * 8);
     const size_t o_sw = take(8);
     const size_t o_stt = take(8);
+    const size_t o_gs = take(size_t(gb) * 8);
+    const size_t o_gw = take(size_t(gb) * 2 * (f64 ? 8 : 4));
     c->off_cr = take(size_t(mb) * 8);
     c->off_sko = take(size_t(mb) * 8);
     // classes
@@ -410,6 +417,9 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     c->st.dens = reinterpret_cast<unsigned long long *>(o_dn);
     c->st.sweep = reinterpret_cast<unsigned long long *>(o_sw);
     c->st.status = reinterpret_cast<unsigned *>(o_stt);
+    c->st.gsig = reinterpret_cast<double *>(o_gs);
+    c->st.gw = reinterpret_cast<void *>(o_gw);
+    c->st.gw_f64 = f64 ? 1 : 0;
     return HQMC_OK;
 }
 
@@ -453,6 +463,8 @@ int prepare(hqmc_ctx *c) {
     s.dens = rebase(s.dens, c->base);
     s.sweep = rebase(s.sweep, c->base);
     s.status = rebase(s.status, c->base);
+    s.gsig = rebase(s.gsig, c->base);
+    s.gw = rebase(s.gw, c->base);
     c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
     c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
     cudaStream_t st = c->stream;
@@ -483,6 +495,15 @@ int prepare(hqmc_ctx *c) {
         HQMC_CUDA(c, cudaMemcpy(c->st.sbits, c->keep_bits.data(), c->keep_bits.size() * 4, cudaMemcpyHostToDevice));
         HQMC_CUDA(c, cudaMemcpy(c->st.x, c->keep_x.data(), c->keep_x.size() * 2, cudaMemcpyHostToDevice));
         HQMC_CUDA(c, cudaMemcpy(c->st.sweep, &c->keep_sweep, 8, cudaMemcpyHostToDevice));
+        if (!c->keep_sig.empty()) {
+            HQMC_CUDA(c, cudaMemcpy(c->st.gsig, c->keep_sig.data(), c->keep_sig.size() * 8, cudaMemcpyHostToDevice));
+            for (int i = 0; i < c->nchains; ++i)
+                if (c->cdev[i].gauss) {
+                    cudaError_t e = launch_gauss_w(c->st, i, c->cdev[i].M, c->cdev[i].N, c->stream);
+                    if (e != cudaSuccess) return cuda_fail(c, e, "gauss_w");
+                }
+            HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
         c->sweeps_host = c->keep_sweep;
         c->started = c->keep_started;
         c->pending_restore = false;
@@ -505,7 +526,12 @@ int stash_state(hqmc_ctx *c) {
     }
     c->keep_bits.resize(sb);
     c->keep_x.resize(xb);
+    long long gtot = 0;
+    for (auto &d : c->cdev)
+        if (d.gauss) gtot = std::max(gtot, d.g_off + ((long long)d.M * d.N + 3) / 4 * 4);
+    c->keep_sig.resize(size_t(gtot));
     HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (gtot) HQMC_CUDA(c, cudaMemcpy(c->keep_sig.data(), c->st.gsig, size_t(gtot) * 8, cudaMemcpyDeviceToHost));
     HQMC_CUDA(c, cudaMemcpy(c->keep_bits.data(), c->st.sbits, sb * 4, cudaMemcpyDeviceToHost));
     HQMC_CUDA(c, cudaMemcpy(c->keep_x.data(), c->st.x, xb * 2, cudaMemcpyDeviceToHost));
     HQMC_CUDA(c, cudaMemcpy(&c->keep_sweep, c->st.sweep, 8, cudaMemcpyDeviceToHost));
@@ -673,6 +699,10 @@ int hqmc_set_params(hqmc_ctx *c, int chain, double t, double U, double beta, dou
         if (rc) return rc;
         if (c->ready && (M != c->ch[i].M || Ns != c->ch[i].Nsig))
             return fail(c, HQMC_ERR_STATE, "M and Nsig are fixed once the state exists");
+        if (c->ready && ((U < 0.0) != (c->ch[i].U < 0.0)))
+            return fail(c, HQMC_ERR_STATE, "the field type (Hirsch for U >= 0, Gaussian for U < 0) is fixed once the state exists");
+        if (U < 0.0 && c->ch[i].L > 32 && c->precision == HQMC_FP64)
+            return fail(c, HQMC_ERR_UNSUPPORTED, "no FP64 form for L > 32");
     }
     for (int i = lo; i < hi; ++i) {
         HostChain &h = c->ch[i];
@@ -698,10 +728,15 @@ int hqmc_set_params(hqmc_ctx *c, int chain, double t, double U, double beta, dou
             d.w_minus[1] = std::exp(d.lam);
             d.t = c->ch[i].t;
             d.beta = c->ch[i].beta;
+            d.gcoup = std::sqrt(std::fabs(c->ch[i].U) * c->ch[i].dtau);
             ChainTab tb;
             build_tab(c->ch[i], tb, d.lam);
             HQMC_CUDA(c, cudaMemcpyAsync((void *)(c->st.chains + i), &d, sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
             HQMC_CUDA(c, cudaMemcpyAsync((void *)(c->st.tabs + i), &tb, sizeof(ChainTab), cudaMemcpyHostToDevice, c->stream));
+            if (d.gauss) {
+                cudaError_t e = launch_gauss_w(c->st, i, d.M, d.N, c->stream);
+                if (e != cudaSuccess) return cuda_fail(c, e, "gauss_w");
+            }
         }
         HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
@@ -951,7 +986,8 @@ int hqmc_get_state(hqmc_ctx *c, int chain, int8_t *s, int32_t *x, int *anchor, u
     int rc = prepare(c);
     if (rc) return rc;
     const ChainDev &d = c->cdev[chain];
-    if (s) {
+    if (s && d.gauss) std::memset(s, 0, size_t(d.M) * d.N);
+    if (s && !d.gauss) {
         std::vector<uint32_t> bits(size_t(d.M) * d.L * d.wpl);
         HQMC_CUDA(c, cudaMemcpyAsync(bits.data(), c->st.sbits + d.s_off, bits.size() * 4, cudaMemcpyDeviceToHost, c->stream));
         HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -981,11 +1017,38 @@ int hqmc_get_state(hqmc_ctx *c, int chain, int8_t *s, int32_t *x, int *anchor, u
     return HQMC_OK;
 }
 
+int hqmc_get_sigma(hqmc_ctx *c, int chain, double *sigma) {
+    if (!c || chain < 0 || chain >= c->nchains || !sigma) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    if (!d.gauss) return fail(c, HQMC_ERR_ARG, "chain has the Hirsch field (U >= 0): use hqmc_get_state");
+    HQMC_CUDA(c, cudaMemcpyAsync(sigma, c->st.gsig + d.g_off, sizeof(double) * d.M * d.N, cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HQMC_OK;
+}
+
+int hqmc_set_sigma(hqmc_ctx *c, int chain, const double *sigma) {
+    if (!c || chain < 0 || chain >= c->nchains || !sigma) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    if (!d.gauss) return fail(c, HQMC_ERR_ARG, "chain has the Hirsch field (U >= 0): use hqmc_set_state");
+    for (long long k = 0; k < (long long)d.M * d.N; ++k)
+        if (!std::isfinite(sigma[k])) return fail(c, HQMC_ERR_ARG, "field values must be finite");
+    HQMC_CUDA(c, cudaMemcpyAsync(c->st.gsig + d.g_off, sigma, sizeof(double) * d.M * d.N, cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = launch_gauss_w(c->st, chain, d.M, d.N, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gauss_w");
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HQMC_OK;
+}
+
 int hqmc_set_state(hqmc_ctx *c, int chain, const int8_t *s, const int32_t *x, const uint64_t *sweeps) {
     if (!c || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
     int rc = prepare(c);
     if (rc) return rc;
     const ChainDev &d = c->cdev[chain];
+    if (s && d.gauss) return fail(c, HQMC_ERR_ARG, "chain has the Gaussian field (U < 0): use hqmc_set_sigma");
     if (s) {
         std::vector<uint32_t> rows(size_t(d.M) * d.L * d.wpl, 0u), cols(rows.size(), 0u);
         for (int l = 0; l < d.M; ++l)

@@ -1,6 +1,8 @@
 // slice.cu -- site-parallel kernels: the Hirsch-field Gibbs resample fused with the
 // observable accumulation (Sec. 3.5.4 and Sec. 4), state initialisation, the sweep
 // counter and the observable read-out.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -45,6 +47,30 @@ __host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl) {
     s.sk = align16(s.tw + size_t(L) * 8);
     s.total = N <= size_t(kSkSmemMaxN) ? align16(s.sk + N * 8) : s.sk;
     return s;
+}
+
+// Gaussian field (U < 0): standard normal by the Box-Muller transform from the two
+// uniforms of j = 2x and 2x+1: z = sqrt(-2 ln(1 - u1)) cos(2 pi u2), in FP64.
+__device__ __forceinline__ double box_muller(uint64_t w1, uint64_t w2) {
+    const double u1 = u53(w1), u2 = u53(w2);
+    return sqrt(-2.0 * log(1.0 - u1)) * cospi(2.0 * u2);
+}
+
+// sigma_{x,l} and its slice potential W = exp(a sigma) in both layouts
+__device__ __forceinline__ void put_gauss(const DevState &st, const ChainDev &cd, int l, int x, double sig) {
+    const int L = cd.L, N = cd.N;
+    const int ix = x % L, iy = x / L;
+    st.gsig[cd.g_off + (long long)l * N + x] = sig;
+    const double w = exp(cd.gcoup * sig);
+    const long long rw = 2 * cd.g_off + (long long)l * N + iy * L + ix;
+    const long long cw = 2 * cd.g_off + (long long)cd.M * N + (long long)l * N + ix * L + iy;
+    if (st.gw_f64) {
+        static_cast<double *>(st.gw)[rw] = w;
+        static_cast<double *>(st.gw)[cw] = w;
+    } else {
+        static_cast<float *>(st.gw)[rw] = float(w);
+        static_cast<float *>(st.gw)[cw] = float(w);
+    }
 }
 
 }  // namespace
@@ -98,7 +124,30 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
     for (int l = l_begin; l < l_end; ++l) {
         int *hu = hu_base + (long long)l * N;
         int *hd = hd_base + (long long)l * N;
-        const int nquads = (N + 3) >> 2;
+        if (cd.gauss) {
+            // Gaussian field: sigma ~ N(a (n_up + n_dn - 1/2), 1), uniforms j = 2x, 2x+1
+            const int npairs = (N + 1) >> 1;
+            for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+                const u64x4 w4 = philox4x64_10((uint64_t)pr, (uint64_t)l, 1, sweep, cd.seed, 0);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int x = 2 * pr + j;
+                    if (x >= N) break;
+                    const int nu = hu[x], nd = hd[x];
+                    hu[x] = 0;
+                    hd[x] = 0;
+                    const int m = nu - nd;
+                    put_gauss(st, cd, l, x, cd.gcoup * (double(nu + nd) - 0.5) + box_muller(w4.v[2 * j], w4.v[2 * j + 1]));
+                    if (measure) {
+                        n_acc += (unsigned long long)(nu + nd);
+                        d_acc += (unsigned long long)(nu * nd);
+                        m2_acc += (unsigned long long)(m * m);
+                        if (do_sk) ms[x] = float(m);
+                    }
+                }
+            }
+        }
+        const int nquads = cd.gauss ? 0 : (N + 3) >> 2;
         for (int qd = threadIdx.x; qd < nquads; qd += blockDim.x) {
             const u64x4 w4 = philox4x64_10((uint64_t)qd, (uint64_t)l, 1, sweep, cd.seed, 0);
 #pragma unroll
@@ -126,7 +175,7 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < L * wpl; k += blockDim.x) {
+        for (int k = threadIdx.x; k < (cd.gauss ? 0 : L * wpl); k += blockDim.x) {
             srow_g[(long long)l * L * wpl + k] = rows[k];
             scol_g[(long long)l * L * wpl + k] = cols[k];
         }
@@ -216,6 +265,16 @@ __global__ void init_fields_kernel(DevState st) {
         }
     }
     __syncthreads();
+    if (cd.gauss) {
+        // standard normal sigma from phase 3 (sweep 2^64-1), uniforms j = 2x, 2x+1
+        for (int l = blockIdx.x; l < M; l += gridDim.x)
+            for (int x = threadIdx.x; x < N; x += blockDim.x) {
+                const u64x4 w4 = philox4x64_10((uint64_t)(x >> 1), (uint64_t)l, 3, ~0ull, cd.seed, 0);
+                const int j = 2 * (x & 1);
+                put_gauss(st, cd, l, x, box_muller(w4.v[j], w4.v[j + 1]));
+            }
+        return;
+    }
     for (int l = blockIdx.x; l < M; l += gridDim.x) {
         for (int x = threadIdx.x; x < N; x += blockDim.x) {
             const u64x4 w4 = philox4x64_10((uint64_t)(x >> 2), (uint64_t)l, 3, ~0ull, cd.seed, 0);
@@ -256,6 +315,20 @@ cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stre
 }
 
 __global__ void advance_kernel(DevState st) { *st.sweep += 1ull; }
+
+// W = exp(a sigma) again for chain c (after a change of a)
+__global__ void gauss_w_kernel(DevState st, int c) {
+    const ChainDev &cd = st.chains[c];
+    const long long MN = (long long)cd.M * cd.N;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < MN; k += (long long)gridDim.x * blockDim.x)
+        put_gauss(st, cd, int(k / cd.N), int(k % cd.N), st.gsig[cd.g_off + k]);
+}
+
+cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStream_t stream) {
+    const long long MN = (long long)M * N;
+    gauss_w_kernel<<<int(std::min<long long>((MN + 255) / 256, 1024)), 256, 0, stream>>>(st, chain);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream) {
     advance_kernel<<<1, 1, 0, stream>>>(st);

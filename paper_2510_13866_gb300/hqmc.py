@@ -39,6 +39,8 @@ SIGNATURES = {
     "hqmc_chain_shape": (_i, [_vp, _i, _vp, _vp, _vp]),
     "hqmc_get_state": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "hqmc_set_state": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "hqmc_get_sigma": (_i, [_vp, _i, _vp]),
+    "hqmc_set_sigma": (_i, [_vp, _i, _vp]),
     "hqmc_set_profiling": (_i, [_vp, _i]),
     "hqmc_profile_read": (_i, [_vp, _vp, _vp, _vp]),
     "hqmc_ffbs_noalloc": (_i, [_i, _i, _i, _d, _d, _d, _u64, _u64, _vp, _vp, _vp, _i, _vp]),
@@ -278,6 +280,20 @@ class Lattice:
         xa = None if x is None else np.ascontiguousarray(x, dtype=np.int32).reshape(2, Ns, M)
         sw = None if sweeps is None else C.byref(C.c_uint64(int(sweeps)))
         self._check(lib().hqmc_set_state(self._ctx, chain, _ptr(sa), _ptr(xa), sw))
+
+    def get_sigma(self, chain):
+        """Gaussian field [M][N] of a U < 0 chain."""
+        self.prepare()
+        L, M, _ = self.shapes[chain]
+        sig = np.zeros((M, L * L))
+        self._check(lib().hqmc_get_sigma(self._ctx, chain, _ptr(sig)))
+        return sig
+
+    def set_sigma(self, chain, sigma):
+        self.prepare()
+        L, M, _ = self.shapes[chain]
+        sig = np.ascontiguousarray(sigma, dtype=np.float64).reshape(M, L * L)
+        self._check(lib().hqmc_set_sigma(self._ctx, chain, _ptr(sig)))
 
     def set_profiling(self, max_sweeps):
         self._check(lib().hqmc_set_profiling(self._ctx, int(max_sweeps)))

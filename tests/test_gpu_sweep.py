@@ -223,7 +223,9 @@ def test_invalid_parameters_are_rejected():
     with pytest.raises(HQMCError):
         lat.set_params(1.0, 4.0, 1.0, 0.3, 1.0)  # beta/dtau not an integer
     with pytest.raises(HQMCError):
-        lat.set_params(1.0, -1.0, 1.0, 0.1, 1.0)  # U < 0
+        lat.set_params(-1.0, 4.0, 1.0, 0.1, 1.0)  # t < 0
+    with pytest.raises(HQMCError):
+        lat.set_params(1.0, float("nan"), 1.0, 0.1, 1.0)  # U not finite
     with pytest.raises(HQMCError):
         lat.set_params(1.0, 4.0, 1.0, 0.1, 0.3)  # filling*N/2 not an integer
     with pytest.raises(HQMCError):
