@@ -36,7 +36,10 @@ def lib():
         L.orc_filter.argtypes = [i, i, vp, vp, i, i, vp]
         L.orc_filter.restype = d
         L.orc_backward.argtypes = [i, i, vp, vp, i, u64, u64, u64, vp, vp]
-        L.orc_sweep.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i]
+        L.orc_filter_block.argtypes = [i, i, vp, vp, i, i, i, i, vp]
+        L.orc_filter_block.restype = d
+        L.orc_backward_block.argtypes = [i, i, vp, vp, i, i, u64, u64, u64, vp, vp]
+        L.orc_sweep.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i, i]
         L.orc_sweep.restype = i
         L.orc_marginals.argtypes = [i, i, vp, vp, vp, i, vp, vp]
         L.orc_marginals.restype = d
@@ -48,7 +51,7 @@ def lib():
         L.orc_gauss_coupling.argtypes = [d, d]
         L.orc_gauss_coupling.restype = d
         L.orc_init_sigma.argtypes = [i, i, u64, vp]
-        L.orc_sweep_gauss.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i]
+        L.orc_sweep_gauss.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i, i]
         L.orc_sweep_gauss.restype = i
         L.orc_num_threads.restype = i
         _lib = L
@@ -133,7 +136,7 @@ class Chain:
     def lam(self):
         return lam(self.U, self.dtau)
 
-    def sweep(self, want_margin=False, nwl_limit=-1):
+    def sweep(self, want_margin=False, nwl_limit=-1, block=0):
         """One sweep; returns a dict with logw, hist, anchor, links (and margin)."""
         M, N, Ns = self.M, self.N, self.Nsig
         logw = np.full((2, Ns), np.nan)
@@ -144,11 +147,11 @@ class Chain:
         if self.gauss:
             lib().orc_sweep_gauss(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
                                   _p(self.sigma), _p(self.x), _p(logw), _p(hist), _p(margin), _p(links),
-                                  C.byref(anchor), nwl_limit)
+                                  C.byref(anchor), nwl_limit, block)
         else:
             lib().orc_sweep(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
                             _p(self.s), _p(self.x), _p(logw), _p(hist), _p(margin), _p(links),
-                            C.byref(anchor), nwl_limit)
+                            C.byref(anchor), nwl_limit, block)
         self.sweep_count += 1
         out = dict(logw=logw, hist=hist, anchor=anchor.value, links=links)
         if want_margin:
@@ -171,6 +174,23 @@ def filter_logz(L, M, g, W, a, xa, want_f=False):
     f = np.zeros((M, L * L)) if want_f else None
     lz = lib().orc_filter(L, M, _p(g), _p(W), a, xa, _p(f))
     return (lz, f) if want_f else lz
+
+
+def filter_block(L, M, g, W, l0, B, xs, xe, want_f=False):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    f = np.zeros((M, L * L)) if want_f else None
+    lz = lib().orc_filter_block(L, M, _p(g), _p(W), l0, B, xs, xe, _p(f))
+    return (lz, f) if want_f else lz
+
+
+def backward_block(L, M, g, f, l0, B, seed, sweep, wl, xpath):
+    xp = np.ascontiguousarray(xpath, dtype=np.int32).copy()
+    margin = np.zeros(M)
+    lib().orc_backward_block(L, M, _p(np.ascontiguousarray(g, dtype=np.float64)),
+                             _p(np.ascontiguousarray(f, dtype=np.float64)), l0, B, seed, sweep, wl,
+                             _p(xp), _p(margin))
+    return xp, margin
 
 
 def backward(L, M, g, f, a, seed, sweep, wl, xpath):

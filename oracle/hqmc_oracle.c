@@ -196,19 +196,21 @@ void orc_init_state(int L, int M, int Nsig, uint64_t seed, int8_t *s, int32_t *x
 /* Forward filter and backward sampling (Sec. 3.5.2, Eq. ffbsFwd)             */
 /* ------------------------------------------------------------------------- */
 
-/* Forward filter of one worldline anchored at slice a, site xa.
- * W is [M][N] (slice potential of this spin).  If f_store is non-NULL it receives
- * f_l = W_l . alpha_l (sum-normalised alpha) for every slice l.
- * Returns log Z = log sum over closed paths with x_a held of prod W G. */
-double orc_filter(int L, int M, const double *g, const double *W, int a, int xa, double *f_store)
+/* Forward filter over the block of B slices l0, l0+1, ..., l0+B-1 (mod M) with the
+ * worldline held at x_{l0} = xs and x_{l0+B} = xe (Sec. 3.5.2: "a block {l0 : l1} with
+ * fixed endpoints").  alpha_{l0} = delta_{xs}; f_l = W_l . alpha_l is stored (if f_store)
+ * at f_store[l]; alpha is sum-normalised after every step.  Returns
+ * log sum over block paths of prod W G = sum log c + log alpha_{l0+B}(xe). */
+double orc_filter_block(int L, int M, const double *g, const double *W, int l0, int B, int xs, int xe,
+                        double *f_store)
 {
     int N = L * L;
     double *alpha = calloc(N, sizeof(double)), *f = malloc(N * sizeof(double)),
            *nxt = malloc(N * sizeof(double));
     double logZ = 0.0;
-    alpha[xa] = 1.0;
-    for (int i = 0; i < M; ++i) {
-        int l = (a + i) % M;
+    alpha[xs] = 1.0;
+    for (int i = 0; i < B; ++i) {
+        int l = (l0 + i) % M;
         for (int x = 0; x < N; ++x) f[x] = W[(size_t)l * N + x] * alpha[x];
         if (f_store) memcpy(f_store + (size_t)l * N, f, N * sizeof(double));
         orc_conv(L, g, f, nxt);
@@ -217,22 +219,29 @@ double orc_filter(int L, int M, const double *g, const double *W, int a, int xa,
         for (int x = 0; x < N; ++x) alpha[x] = nxt[x] / c;
         logZ += log(c);
     }
-    logZ += log(alpha[xa]);
+    logZ += log(alpha[xe]);
     free(alpha); free(f); free(nxt);
     return logZ;
 }
 
-/* Backward sampling of one worldline given the stored f_l: for i = M-1..1,
- * l = (a+i) mod M, draw x_l from p(y) ~ f_l(y) G(x_{l+1} - y) by the row-major
- * inverse CDF: the smallest y with u*S < C(y).  margin[l] (optional) receives the
- * distance from u*S to the nearer edge of the chosen CDF interval, over S. */
-void orc_backward(int L, int M, const double *g, const double *f_store, int a,
-                  uint64_t seed, uint64_t sweep, uint64_t wl, int32_t *xpath, double *margin)
+/* Forward filter of the closed loop of one worldline anchored at slice a, site xa:
+ * the block of all M slices with both ends at xa. */
+double orc_filter(int L, int M, const double *g, const double *W, int a, int xa, double *f_store)
+{
+    return orc_filter_block(L, M, g, W, a, M, xa, xa, f_store);
+}
+
+/* Backward sampling of the block's interior given the stored f_l and x_{l0+B} (already in
+ * xpath): for i = B-1..1, l = (l0+i) mod M, draw x_l from p(y) ~ f_l(y) G(x_{l+1} - y) by
+ * the row-major inverse CDF, the smallest y with u*S < C(y).  margin[l] (optional)
+ * receives the distance from u*S to the nearer edge of the chosen CDF interval, over S. */
+void orc_backward_block(int L, int M, const double *g, const double *f_store, int l0, int B,
+                        uint64_t seed, uint64_t sweep, uint64_t wl, int32_t *xpath, double *margin)
 {
     int N = L * L;
     double *p = malloc(N * sizeof(double));
-    for (int i = M - 1; i >= 1; --i) {
-        int l = (a + i) % M, next = xpath[(l + 1) % M];
+    for (int i = B - 1; i >= 1; --i) {
+        int l = (l0 + i) % M, next = xpath[(l + 1) % M];
         double S = 0.0;
         for (int y = 0; y < N; ++y) {
             p[y] = f_store[(size_t)l * N + y] * orc_G(g, L, y, next);
@@ -253,8 +262,15 @@ void orc_backward(int L, int M, const double *g, const double *f_store, int a,
             margin[l] = (S > 0.0) ? (m1 < m2 ? m1 : m2) / S : 0.0;
         }
     }
-    if (margin) margin[a] = INFINITY; /* the anchor is held, not drawn */
+    if (margin) margin[l0 % M] = INFINITY; /* the block's start is held, not drawn */
     free(p);
+}
+
+/* Backward sampling of the closed loop anchored at slice a. */
+void orc_backward(int L, int M, const double *g, const double *f_store, int a,
+                  uint64_t seed, uint64_t sweep, uint64_t wl, int32_t *xpath, double *margin)
+{
+    orc_backward_block(L, M, g, f_store, a, M, seed, sweep, wl, xpath, margin);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -271,13 +287,17 @@ void orc_backward(int L, int M, const double *g, const double *f_store, int a,
  *   anchor receives the anchor slice (nullable).
  *   nwl_limit: if >= 0, only the first nwl_limit worldlines of each spin are
  *   resampled (a bounded sample for timing); the Gibbs step is then skipped.
+ *   block: FFBS block length B (0 or >= M: the whole loop from the anchor); with B < M
+ *   the loop is resampled block by block from the anchor, each with its ends held. 
  * Worldlines are independent given s, so they are processed in parallel. */
 /* FFBS of every worldline (the first nwl of each spin) given the slice potentials
  * W [2][M][N] (spin-major): anchor, filter, backward draw, link sums. */
 static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
                         uint64_t seed, uint64_t sweep, int32_t *xpath, double *logw, double *margin,
-                        double *links, int *anchor, int nwl)
+                        double *links, int *anchor, int nwl, int block)
 {
+    int B = (block > 0 && block < M) ? block : M;
+    int nblk = (M + B - 1) / B;
     int N = L * L;
     int a = (int)floor(orc_uniform(seed, sweep, 2, 0, 0) * M);
     if (a >= M) a = M - 1;
@@ -291,9 +311,16 @@ static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *d
         uint64_t wl = (uint64_t)sg * Nsig + p;
         int32_t *xp = xpath + wl * M;
         double *fst = malloc((size_t)M * N * sizeof(double));
-        double lz = orc_filter(L, M, g, W + (size_t)sg * M * N, a, xp[a], fst);
+        /* blocks a, a+B, a+2B, ... (the last one may be shorter), resampled in turn with
+         * their end sites held; the log-weight is the sum of the blocks' */
+        double lz = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            int l0 = (a + b * B) % M, len = (b + 1) * B <= M ? B : M - b * B;
+            int xs = xp[l0], xe = xp[(l0 + len) % M];
+            lz += orc_filter_block(L, M, g, W + (size_t)sg * M * N, l0, len, xs, xe, fst);
+            orc_backward_block(L, M, g, fst, l0, len, seed, sweep, wl, xp, margin ? margin + wl * M : NULL);
+        }
         if (logw) logw[wl] = lz;
-        orc_backward(L, M, g, fst, a, seed, sweep, wl, xp, margin ? margin + wl * M : NULL);
         if (links) {
             double acc = 0.0;
             for (int l = 0; l < M; ++l) {
@@ -321,7 +348,7 @@ static void orc_histogram(int L, int M, int Nsig, const int32_t *xpath, int32_t 
 
 int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
               int8_t *s, int32_t *xpath, double *logw, int32_t *hist, double *margin,
-              double *links, int *anchor, int nwl_limit)
+              double *links, int *anchor, int nwl_limit, int block)
 {
     int N = L * L;
     double lam = orc_lambda(U, dtau);
@@ -335,7 +362,7 @@ int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t 
                 W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
     }
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
-    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl);
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);
@@ -389,7 +416,7 @@ void orc_init_sigma(int L, int M, uint64_t seed, double *sigma)
  * j = 2x, 2x+1. */
 int orc_sweep_gauss(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
                     double *sigma, int32_t *xpath, double *logw, int32_t *hist, double *margin,
-                    double *links, int *anchor, int nwl_limit)
+                    double *links, int *anchor, int nwl_limit, int block)
 {
     int N = L * L;
     double a = orc_gauss_coupling(U, dtau);
@@ -401,7 +428,7 @@ int orc_sweep_gauss(int L, int M, int Nsig, double t, double U, double dtau, uin
             for (int x = 0; x < N; ++x)
                 W[((size_t)sg * M + l) * N + x] = exp(a * sigma[(size_t)l * N + x]);
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
-    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl);
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);

@@ -195,6 +195,61 @@ def test_filter_and_backward_vs_enumeration(orc):
     assert chi2 < dof + 5.3 * math.sqrt(2 * dof), (chi2, dof)
 
 
+def test_block_filter_and_backward_vs_enumeration(orc):
+    """A block {l0 : l0+B} with both end sites held (Sec. 3.5.2): brute force over all 9^2
+    interior paths (L=3, B=3 inside M=5, wrapping past slice M-1): log Z of the block and
+    the law of the drawn interior (chi^2)."""
+    L, M, B, dtau, U = 3, 5, 3, 0.5, 4.0
+    N = L * L
+    g, _ = orc.g_table(L, 1.0, dtau)
+    lam = orc.lam(U, dtau)
+    rng = np.random.default_rng(5)
+    W = np.exp(lam * rng.choice([-1, 1], size=(M, N)))
+    l0, xs, xe = 3, 2, 7  # slices 3, 4, 0 and the held site at slice 1
+    inner = [(l0 + i) % M for i in range(1, B)]
+    paths, weights = [], []
+    for combo in itertools.product(range(N), repeat=B - 1):
+        x = {l0: xs, (l0 + B) % M: xe}
+        x.update(zip(inner, combo))
+        w = 1.0
+        for i in range(B):
+            l = (l0 + i) % M
+            y0, y1 = x[l], x[(l + 1) % M]
+            w *= W[l][y0] * g[(y1 % L - y0 % L) % L] * g[(y1 // L - y0 // L) % L]
+        paths.append(combo)
+        weights.append(w)
+    weights = np.array(weights)
+    lz, f = orc.filter_block(L, M, g, W, l0, B, xs, xe, want_f=True)
+    assert abs(lz - math.log(weights.sum())) < 1e-12 * abs(math.log(weights.sum()))
+    prob = weights / weights.sum()
+    index = {p: k for k, p in enumerate(paths)}
+    counts = np.zeros(len(paths))
+    n = 20000
+    x0 = np.zeros(M, dtype=np.int32)
+    x0[l0], x0[(l0 + B) % M] = xs, xe
+    for sweep in range(n):
+        xp, margin = orc.backward_block(L, M, g, f, l0, B, 17, sweep, 0, x0)
+        assert xp[l0] == xs and xp[(l0 + B) % M] == xe  # the ends are held
+        counts[index[tuple(int(xp[l]) for l in inner)]] += 1
+    expected = prob * n
+    big = expected >= 5
+    chi2 = (((counts - expected) ** 2) / expected)[big].sum()
+    rest_o, rest_e = counts[~big].sum(), expected[~big].sum()
+    chi2 += (rest_o - rest_e) ** 2 / max(rest_e, 1e-9)
+    dof = big.sum()
+    assert chi2 < dof + 5.3 * math.sqrt(2 * dof), (chi2, dof)
+
+
+def test_sweep_block_equals_loop_when_block_covers_it(orc):
+    """B >= M is the closed-loop FFBS from the anchor: identical chains."""
+    a = orc.Chain(L=4, t=1.0, U=4.0, beta=1.0, dtau=0.1, filling=1.0, seed=8)
+    b = orc.Chain(L=4, t=1.0, U=4.0, beta=1.0, dtau=0.1, filling=1.0, seed=8)
+    for _ in range(3):
+        ra, rb = a.sweep(), b.sweep(block=10)
+        assert np.array_equal(ra["logw"], rb["logw"])
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.s, b.s)
+
+
 def test_backward_inverse_cdf_rule(orc):
     """The drawn site is the smallest y with u*S < C(y) (row-major), checked by hand."""
     L, M = 3, 3
@@ -322,6 +377,29 @@ def test_sweep_two_particle_exact(orc):
     Ds, Es = [], []
     for k in range(24000):
         out = ch.sweep()
+        if k < 500:
+            continue
+        m = orc.measure(L, M, out["hist"], want_fields=False)
+        Ds.append(m["d"] / (M * L * L))
+        Es.append(-(1.0 / beta) * out["links"].sum() / (L * L))
+    dm, de = _batch_stats(Ds)
+    em, ee = _batch_stats(Es)
+    assert abs(dm - D_ex) < 4.5 * de + 1e-4, (dm, de, D_ex)
+    assert abs(em - E_ex) < 4.5 * ee + 1e-4, (em, ee, E_ex)
+
+
+@pytest.mark.parametrize("block", [2, 3])
+def test_sweep_two_particle_exact_blocks(orc, block):
+    """Block FFBS (B < M, block ends held) + Gibbs still samples the exact two-particle
+    measure: D and E_kin against the transfer matrix (M = 4).  (B = 1 has no interior
+    slice: it moves no worldline and is not ergodic.)"""
+    L, U, dtau, beta = 3, 4.0, 0.25, 1.0
+    M = 4
+    D_ex, E_ex = two_particle_exact(L, 1.0, U, dtau, M)
+    ch = orc.Chain(L=L, t=1.0, U=U, beta=beta, dtau=dtau, filling=2.0 / (L * L), seed=9 + block)
+    Ds, Es = [], []
+    for k in range(24000):
+        out = ch.sweep(block=block)
         if k < 500:
             continue
         m = orc.measure(L, M, out["hist"], want_fields=False)
