@@ -158,7 +158,7 @@ def run_grad(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    nch = args.chains if args.chains != WORK["chains"] else 128
+    nch = args.chains or 128
     p = (1.0, 4.0, 4.0, 0.05, 1.0)
     lat = Lattice(16, chain_seeds(rank, nch), precision="fp32", device=local)
     lat.set_params(*p)
@@ -217,6 +217,9 @@ WORKLOADS = {
                "{0.5,0.875,1}, dtau=0.05, drawn per chain from Philox key (1,0); one graph replay per sweep"),
     "L64": "2D Hubbard L=64 (N=4096) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
     "L128": "2D Hubbard L=128 (N=16384) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
+    "paper8": "the paper's timing regime: L=8, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
+    "paper16": "the paper's timing regime: L=16, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
+    "paper32": "the paper's timing regime: L=32, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
 }
 
 
@@ -226,15 +229,19 @@ def workload(name, rank, chains, beta=None):
     from paper_2510_13866_gb300.workloads import ragged
 
     if name == "L32":
-        n = chains
+        n = chains or WORK["chains"]
         p = (WORK["t"], WORK["U"], WORK["beta"], WORK["dtau"], WORK["filling"])
         return [32] * n, [p] * n, chain_seeds(rank, n)
     if name == "ragged":
-        n = chains if chains != WORK["chains"] else 256
+        n = chains or 256
         work = ragged(n)
         return [w[0] for w in work], [w[1] for w in work], chain_seeds(rank, n)
+    if name.startswith("paper"):
+        L = int(name[5:])
+        n = chains or 1
+        return [L] * n, [(1.0, 4.0, 32.0, 1.0 / 32.0, 1.0)] * n, chain_seeds(rank, n)
     L = int(name[1:])
-    n = chains if chains != WORK["chains"] else 16
+    n = chains or 16
     return [L] * n, [(1.0, 4.0, beta if beta else 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
 
 
@@ -258,10 +265,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS) + ["grad16"],
-                    help="L32 (default, the headline configuration), ragged, L64, L128; grad16 times the adjoint")
+                    help="L32 (default, the headline configuration), ragged, L64, L128, paper8/16/32 "
+                         "(M=1024); grad16 times the adjoint")
+    ap.add_argument("--block", type=int, default=0,
+                    help="FFBS block length B (0: the closed loop from the anchor, the default)")
     ap.add_argument("--beta", type=float, default=None,
                     help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures)")
-    ap.add_argument("--chains", type=int, default=WORK["chains"],
+    ap.add_argument("--chains", type=int, default=None,
                     help="chains per GPU (default: the workload's own; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -305,6 +315,8 @@ def main():
         else:
             for c, p in enumerate(pars):
                 lt.set_params(*p, chain=c)
+        if args.block:
+            lt.set_block(args.block)
         lt.prepare()
         return lt
 
@@ -411,13 +423,18 @@ def main():
         wl = WORKLOADS[args.workload]
         if args.workload == "L32" and nchains != WORK["chains"]:
             wl = wl.replace("x 64 chains", f"x {nchains} chains")
+        if args.workload.startswith("paper") and nchains != 1:
+            wl = wl.replace("1 chain", f"{nchains} chains")
+        if args.block:
+            wl += f"; block FFBS, B={args.block}"
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl, "L": sorted(set(Ls)) if nclasses > 1 else Ls[0],
                            "M": sorted(set(M for _, M, _ in shapes)) if nclasses > 1 else shapes[0][1],
                            "chains_per_gpu": nchains, "parallelism": f"chains sharded over {world} GPU(s)",
-                           "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2; no flush needed"},
+                           "l2": "per-sweep working set (f-message scratch, GBs) exceeds L2; no flush needed"
+                           if not args.block else "FFBS blocks: the f-message working set is B slices per group"},
                 "particle_slice_updates_per_s": value * part_slices,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (nclasses + 2), "clocks": clocks, "fp64_plain": fp64,

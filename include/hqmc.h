@@ -103,6 +103,24 @@ int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t
 int hqmc_set_params(hqmc_ctx *ctx, int chain, double t, double U, double beta, double dtau,
                     double filling);
 
+/* FFBS block length B of one chain (chain = -1: all chains).  B = 0, or B >= M, resamples
+ * each worldline as the closed loop of M slices from the anchor slice a with x_a held
+ * (the default).  1 <= B < M resamples it block by block (Sec. 3.5.2, a block of slices
+ * with fixed endpoints): the blocks start at a, a+B, a+2B, ... (mod M), the last one
+ * ends at a and may be shorter, and each block's interior slices are drawn given its two
+ * end sites, which keep their current values.  The sweep's log-weight of a worldline is
+ * then the sum over its blocks of log sum_{paths inside} prod W G, each block's filter
+ * started from delta at its first site and read at its last.  The blocks of a worldline
+ * pair are independent work units of the FFBS launch (they share no slice but the held
+ * ends), so a long loop spreads over many SMs; the partial log-weights are summed in
+ * block order, which gives the same bits as resampling the blocks one after another.
+ * Both kernels (L <= 32 and wide) and both precisions take it; the no-allocation entry
+ * point always uses B = M.  A change of B re-lays the context out at its next use as
+ * described at hqmc_set_class_launch (state kept, observable accumulators restart, an
+ * attached workspace must be attached again).  Errors: HQMC_ERR_ARG (chain out of range,
+ * B < 0), HQMC_ERR_CUDA. */
+int hqmc_set_block(hqmc_ctx *ctx, int chain, int B);
+
 /* CUDA stream (a cudaStream_t passed as void*) on which every later call is ordered;
  * NULL = the legacy default stream.  Changing it drops the captured sweep graph. */
 int hqmc_set_stream(hqmc_ctx *ctx, void *stream);

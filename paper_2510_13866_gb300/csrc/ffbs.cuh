@@ -42,7 +42,8 @@ struct FfbsGeo {
     static constexpr size_t G2B = a16(size_t(2 * L) * sizeof(T));
     static constexpr size_t WXB = a16(size_t(L) * sizeof(V));
     static constexpr size_t RBB = a16(size_t(2 * L) * sizeof(V));  // crossing rows of both worldlines
-    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB + RBB;
+    static constexpr size_t METAB = 32;  // the work unit's block bookkeeping
+    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB + RBB + METAB;
 };
 
 // Target u*S of an inverse-CDF draw from the Philox word w, in the CDF's precision.
@@ -152,32 +153,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     T *g2 = reinterpret_cast<T *>(gsm + G::XBUF + G::MIXB);
     V *wx = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B);
     V *rb = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB);  // [2][L]
+    // block bookkeeping of the current unit (b, nblk, pair, l0, l0+len), parked in shared
+    // memory across the forward loop instead of in registers
+    volatile int *meta = reinterpret_cast<volatile int *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB + G::RBB);
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
     const long long ngroups = (long long)gridDim.x * wpc * G::GPW;
     V *slot = reinterpret_cast<V *>(fl.scratch) + gid * fl.slot_elems;
     const uint64_t sweep = *st.sweep;
 
-    // pairs are taken from a work counter (classes list their chains by decreasing M, so
-    // the longest pairs go first and the tail is short)
+    // work units (pair, block) are taken from a work counter (classes list their chains by
+    // decreasing block length, so the longest units go first and the tail is short)
     (void)ngroups;
     for (;;) {
         unsigned qn = 0;
-        if (gl == 0) qn = atomicAdd(fl.next_pair, 1u);
+        if (gl == 0) qn = atomicAdd(fl.next_unit, 1u);
         const long long q = (long long)__shfl_sync(gmask, qn, 0, GW);
-        if (q >= fl.total_pairs) break;
+        if (q >= fl.total_units) break;
         // ---- locate the pair: chain, spin, worldlines ----
         int lo = 0, hi = fl.nclass - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (fl.class_pair_off[mid] <= q) lo = mid;
+            if (fl.class_unit_off[mid] <= q) lo = mid;
             else hi = mid - 1;
         }
         const int c = fl.class_chains[lo];
         const ChainDev &cd = st.chains[c];
         const ChainTab &tb = st.tabs[c];
         const int M = cd.M, Nsig = cd.Nsig;
-        const int rr = int(q - fl.class_pair_off[lo]);
-        const int sg = rr / cd.npair, kp = rr % cd.npair;
+        // unit = (pair, block): the blocks of a pair are independent given their held ends
+        const int ru = int(q - fl.class_unit_off[lo]);
+        int sg, kp, len;
+        {
+            const int Bk = ffbs_block_len(cd.block, M), nblk = ffbs_nblk(cd.block, M);
+            const int rr = ru / nblk, b = ru - rr * nblk;
+            sg = rr / cd.npair;
+            kp = rr % cd.npair;
+            // block b of the blocks of Bk slices from the anchor a, a+Bk, a+2Bk, ... (the
+            // last may be shorter), resampled with its two end sites held; the log-weight
+            // is the sum of the blocks'.  Bk = M is the closed loop with both ends at x_a.
+            const u64x4 ua = philox4x64_10(0, 0, 2, sweep, cd.seed, 0);  // anchor (phase 2)
+            int a = int(u53(ua.v[0]) * M);
+            if (a >= M) a = M - 1;
+            if (ru == 0 && gl == 0) st.anchor[c] = a;
+            int l0 = a + b * Bk;
+            if (l0 >= M) l0 -= M;
+            len = (b + 1) * Bk <= M ? Bk : M - b * Bk;
+            const int le = (l0 + len >= M) ? l0 + len - M : l0 + len;
+            __syncwarp(gmask);
+            if (gl == 0) {
+                meta[0] = b;
+                meta[1] = nblk;
+                meta[2] = rr;
+                meta[3] = l0;
+                meta[4] = le;
+            }
+        }
         const int p0 = 2 * kp, p1 = 2 * kp + 1;
         const bool has1 = p1 < Nsig;
         const uint64_t wl0 = (uint64_t)sg * Nsig + p0, wl1 = (uint64_t)sg * Nsig + p1;
@@ -197,37 +227,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         }
         __syncwarp(gmask);
 
-        // ---- anchor slice (phase 2) ----
-        const u64x4 ua = philox4x64_10(0, 0, 2, sweep, cd.seed, 0);
-        int a = int(u53(ua.v[0]) * M);
-        if (a >= M) a = M - 1;
-        if (rr == 0 && gl == 0) st.anchor[c] = a;
-        const int xa0 = xp0[a];
-        const int xa1 = has1 ? int(xp1[a]) : xa0;  // a missing partner shadows worldline 0
-        const int ax0 = xa0 % L, ay0 = xa0 / L, ax1 = xa1 % L, ay1 = xa1 / L;
-
         // ---- forward filter ----
+        __syncwarp(gmask);
+        const int l0 = meta[3];
         V v[L];
         {
-            // f_a = W_a(x_a) delta_{x_a}, layout R: lane = iy, register = ix
+            // the held end sites are re-read where they are used (short live ranges)
+            const int xs0 = xp0[l0];
+            const int xs1 = has1 ? int(xp1[l0]) : xs0;  // a missing partner shadows worldline 0
+            const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
+            // f_{l0} = W_{l0}(x_{l0}) delta_{x_{l0}}, layout R: lane = iy, register = ix
             T wv0, wv1;
             if (cd.gauss) {
-                wv0 = gauss_line<T>(st, cd, false, a, ay0)[ax0];
-                wv1 = gauss_line<T>(st, cd, false, a, ay1)[ax1];
+                wv0 = gauss_line<T>(st, cd, false, l0, sy0)[sx0];
+                wv1 = gauss_line<T>(st, cd, false, l0, sy1)[sx1];
             } else {
-                wv0 = ((srow[((long long)a * L + ay0) * cd.wpl + (ax0 >> 5)] >> (ax0 & 31)) & 1u) ? wp : wm;
-                wv1 = ((srow[((long long)a * L + ay1) * cd.wpl + (ax1 >> 5)] >> (ax1 & 31)) & 1u) ? wp : wm;
+                wv0 = ((srow[((long long)l0 * L + sy0) * cd.wpl + (sx0 >> 5)] >> (sx0 & 31)) & 1u) ? wp : wm;
+                wv1 = ((srow[((long long)l0 * L + sy1) * cd.wpl + (sx1 >> 5)] >> (sx1 & 31)) & 1u) ? wp : wm;
             }
 #pragma unroll
             for (int r = 0; r < L; ++r) {
-                v[r].x = (gl == ay0 && r == ax0) ? wv0 : T(0);
-                v[r].y = (gl == ay1 && r == ax1) ? wv1 : T(0);
+                v[r].x = (gl == sy0 && r == sx0) ? wv0 : T(0);
+                v[r].y = (gl == sy1 && r == sx1) ? wv1 : T(0);
             }
         }
         int esum0 = 0, esum1 = 0;
         T fin0 = T(0), fin1 = T(0);
-        int l = a;
-        for (int i = 0; i < M; ++i) {
+        int l = l0;
+        for (int i = 0; i < len; ++i) {
             // f_l of slice i, in the writer's layout: chunk j*L + lane holds registers CH*j..
             if (i >= 1 && active) {
                 V *dst = slot + (long long)i * N;
@@ -278,7 +305,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             T s0 = group_sum<GW>(s.x, gmask);
             T s1 = group_sum<GW>(s.y, gmask);
             const int l1 = (l + 1 == M) ? 0 : l + 1;
-            if (i < M - 1) {
+            if (i < len - 1) {
                 int e0 = 0, e1 = 0;
                 if (s0 > T(0) && s0 < T(1e30)) e0 = fbits<T>::exponent(s0);
                 else if (gl == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
@@ -297,10 +324,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                     for (int r = 0; r < L; ++r) v[r] = vmul(v[r], ((w >> r) & 1u) ? A : B);
                 }
             } else {
-                // alpha_M(x_a): final layout is C if M is odd
-                const bool finC = (M & 1) != 0;
-                const int own0 = finC ? ax0 : ay0, reg0 = finC ? ay0 : ax0;
-                const int own1 = finC ? ax1 : ay1, reg1 = finC ? ay1 : ax1;
+                // alpha_{l0+len}(x_{l0+len}): final layout is C if len is odd
+                const bool finC = (len & 1) != 0;
+                const int le = meta[4];
+                const int xe0 = xp0[le];
+                const int xe1 = has1 ? int(xp1[le]) : xe0;
+                const int ex0 = xe0 % L, ey0 = xe0 / L, ex1 = xe1 % L, ey1 = xe1 / L;
+                const int own0 = finC ? ex0 : ey0, reg0 = finC ? ey0 : ex0;
+                const int own1 = finC ? ex1 : ey1, reg1 = finC ? ey1 : ex1;
                 const T c0 = reg_select<L>(v, reg0).x;
                 const T c1 = reg_select<L>(v, reg1).y;
                 fin0 = __shfl_sync(gmask, c0, own0, GW);
@@ -309,13 +340,35 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             l = l1;
         }
         if (gl == 0) {
+            // log-weight of the block; with several blocks, the pair's last finished block
+            // sums the partials in block order (the same bits whichever finishes last)
             const double ln2 = 0.69314718055994530942;
-            const double lz0 = double(esum0) * ln2 + log(double(fin0));
-            st.logw[cd.logw_off + wl0] = lz0;
+            const double part0 = double(esum0) * ln2 + log(double(fin0));
+            const double part1 = double(esum1) * ln2 + log(double(fin1));
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
-            if (has1) {
-                st.logw[cd.logw_off + wl1] = double(esum1) * ln2 + log(double(fin1));
-                if (!(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
+            if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
+            double *lw = st.logw + cd.logw_off;
+            const int b = meta[0], nblk = meta[1], rr = meta[2];
+            if (nblk == 1) {
+                lw[wl0] = part0;
+                if (has1) lw[wl1] = part1;
+            } else {
+                double *lp = st.logw_part + cd.lwp_off;
+                lp[wl0 * nblk + b] = part0;
+                if (has1) lp[wl1 * nblk + b] = part1;
+                __threadfence();
+                unsigned *done = st.blk_done + cd.done_off + rr;
+                if (atomicAdd(done, 1u) == unsigned(nblk - 1)) {
+                    __threadfence();
+                    double s0 = 0.0, s1 = 0.0;
+                    for (int k = 0; k < nblk; ++k) {
+                        s0 += __ldcg(lp + wl0 * nblk + k);
+                        if (has1) s1 += __ldcg(lp + wl1 * nblk + k);
+                    }
+                    lw[wl0] = s0;
+                    if (has1) lw[wl1] = s1;
+                    *done = 0u;  // ready for the next sweep
+                }
             }
         }
 
@@ -332,19 +385,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             cp_async_commit();
         };
         __syncwarp(gmask);
-        if (M > 1) prefetch(M - 1);
+        if (len > 1) prefetch(len - 1);
         const float *hl = tb.h_f;
-        int cur0 = xa0, cur1 = xa1;
-        float ek0 = 0.f, ek1 = 0.f;
         int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
+        float ek0 = 0.f, ek1 = 0.f;
+        const int le = meta[4];
+        const int xs0 = xp0[l0];
+        const int xs1 = has1 ? int(xp1[l0]) : xs0;
+        const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
+        int cur0 = xp0[le];
+        int cur1 = has1 ? int(xp1[le]) : cur0;
         if (gl == 0) {
-            atomicAdd(hist_s + (long long)a * N + xa0, 1);
-            if (has1) atomicAdd(hist_s + (long long)a * N + xa1, 1);
+            atomicAdd(hist_s + (long long)l0 * N + xs0, 1);
+            if (has1) atomicAdd(hist_s + (long long)l0 * N + xs1, 1);
         }
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
-        for (int i = M - 1; i >= 1; --i) {
-            int lb = a + i;
+        for (int i = len - 1; i >= 1; --i) {
+            int lb = l0 + i;
             if (lb >= M) lb -= M;
             // row gl of f_l (lane = iy, register = ix)
             cp_async_wait_all();
@@ -506,9 +564,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             cur1 = nxt1;
         }
         if (gl == 0) {
-            // link x_a -> x_{a+1}
-            ek0 += hl[(cur0 % L - ax0 + L) % L] + hl[(cur0 / L - ay0 + L) % L];
-            if (has1) ek1 += hl[(cur1 % L - ax1 + L) % L] + hl[(cur1 / L - ay1 + L) % L];
+            // link x_{l0} -> x_{l0+1}
+            ek0 += hl[(cur0 % L - sx0 + L) % L] + hl[(cur0 / L - sy0 + L) % L];
+            if (has1) ek1 += hl[(cur1 % L - sx1 + L) % L] + hl[(cur1 / L - sy1 + L) % L];
             atomicAdd(&st.meas[c].link_sum, double(ek0) + (has1 ? double(ek1) : 0.0));
         }
         __syncwarp(gmask);

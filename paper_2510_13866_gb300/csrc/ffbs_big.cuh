@@ -194,24 +194,27 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         for (int w = 0; w < (L + 31) / 32; ++w) wb[w] = base[((long long)l * L + line) * wpl + w];
     };
 
-    // pairs are taken from a work counter, longest chains first
+    // work units (pair, block) are taken from a work counter, longest blocks first
     for (;;) {
         __syncthreads();
-        if (tid == 0) ibuf[4] = int(atomicAdd(fl.next_pair, 1u));
+        if (tid == 0) ibuf[4] = int(atomicAdd(fl.next_unit, 1u));
         __syncthreads();
         const long long q = ibuf[4];
-        if (q >= fl.total_pairs) break;
+        if (q >= fl.total_units) break;
         int lo = 0, hi = fl.nclass - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (fl.class_pair_off[mid] <= q) lo = mid;
+            if (fl.class_unit_off[mid] <= q) lo = mid;
             else hi = mid - 1;
         }
         const int c = fl.class_chains[lo];
         const ChainDev &cd = st.chains[c];
         const ChainTab &tb = st.tabs[c];
         const int M = cd.M, Nsig = cd.Nsig;
-        const int rr = int(q - fl.class_pair_off[lo]);
+        // unit = (pair, block): the blocks of a pair are independent given their held ends
+        const int Bk = ffbs_block_len(cd.block, M), nblk = ffbs_nblk(cd.block, M);
+        const int ru = int(q - fl.class_unit_off[lo]);
+        const int rr = ru / nblk, b = ru - rr * nblk;
         const int sg = rr / cd.npair, kp = rr % cd.npair;
         const int p0 = 2 * kp, p1 = 2 * kp + 1;
         const bool has1 = p1 < Nsig;
@@ -235,33 +238,44 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         const u64x4 ua = philox4x64_10(0, 0, 2, sweep, cd.seed, 0);
         int a = int(u53(ua.v[0]) * M);
         if (a >= M) a = M - 1;
-        if (rr == 0 && tid == 0) st.anchor[c] = a;
-        const int xa0 = xp0[a];
-        const int xa1 = has1 ? int(xp1[a]) : xa0;
-        const int ax0 = xa0 % L, ay0 = xa0 / L, ax1 = xa1 % L, ay1 = xa1 / L;
+        if (ru == 0 && tid == 0) st.anchor[c] = a;
+
+        // block b of Bk slices from the anchor, resampled with its two end sites held
+        // (Bk = M: the closed loop); the log-weight is the sum of the blocks'
+        const float *hl = tb.h_f;
+        int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
+        float ek0 = 0.f, ek1 = 0.f;
+        int l0 = a + b * Bk;
+        if (l0 >= M) l0 -= M;
+        const int len = (b + 1) * Bk <= M ? Bk : M - b * Bk;
+        const int le = (l0 + len >= M) ? l0 + len - M : l0 + len;
 
         // ---- forward filter ----
+        __syncthreads();
         V v[E];
         {
+            const int xs0 = xp0[l0];
+            const int xs1 = has1 ? int(xp1[l0]) : xs0;
+            const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
             T wv0, wv1;
             if (cd.gauss) {
-                wv0 = gauss_line<T>(st, cd, false, a, ay0)[ax0];
-                wv1 = gauss_line<T>(st, cd, false, a, ay1)[ax1];
+                wv0 = gauss_line<T>(st, cd, false, l0, sy0)[sx0];
+                wv1 = gauss_line<T>(st, cd, false, l0, sy1)[sx1];
             } else {
-                wv0 = ((srow[((long long)a * L + ay0) * wpl + (ax0 >> 5)] >> (ax0 & 31)) & 1u) ? wp : wm;
-                wv1 = ((srow[((long long)a * L + ay1) * wpl + (ax1 >> 5)] >> (ax1 & 31)) & 1u) ? wp : wm;
+                wv0 = ((srow[((long long)l0 * L + sy0) * wpl + (sx0 >> 5)] >> (sx0 & 31)) & 1u) ? wp : wm;
+                wv1 = ((srow[((long long)l0 * L + sy1) * wpl + (sx1 >> 5)] >> (sx1 & 31)) & 1u) ? wp : wm;
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int pos = big_pos<L>(e, s);
-                v[e].x = (active && p == ay0 && pos == ax0) ? wv0 : T(0);
-                v[e].y = (active && p == ay1 && pos == ax1) ? wv1 : T(0);
+                v[e].x = (active && p == sy0 && pos == sx0) ? wv0 : T(0);
+                v[e].y = (active && p == sy1 && pos == sx1) ? wv1 : T(0);
             }
         }
         int esum0 = 0, esum1 = 0;
         T fin0 = T(0), fin1 = T(0);
-        int l = a;
-        for (int i = 0; i < M; ++i) {
+        int l = l0;
+        for (int i = 0; i < len; ++i) {
             if (i >= 1 && active) {
                 float4 *dst = reinterpret_cast<float4 *>(slot + (long long)i * N);
 #pragma unroll
@@ -297,7 +311,7 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             const V tsum = block_sum(sm);
             const T s0 = tsum.x, s1 = tsum.y;
             const int l1 = (l + 1 == M) ? 0 : l + 1;
-            if (i < M - 1) {
+            if (i < len - 1) {
                 int e0 = 0, e1 = 0;
                 if (s0 > T(0) && s0 < T(1e30)) e0 = fbits<T>::exponent(s0);
                 else if (tid == 0) atomicAdd(&st.meas[c].degenerate, 1ull);
@@ -321,10 +335,13 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
                     for (int e = 0; e < E; ++e) v[e] = vmul(v[e], ((wb[big_word<L>(e)] >> big_bit<L>(e, s)) & 1u) ? A : Bv);
                 }
             } else {
-                // alpha_M(x_a): final layout is C (lines = x) if M is odd
-                const bool finC = (M & 1) != 0;
-                const int own0 = finC ? ax0 : ay0, pos0 = finC ? ay0 : ax0;
-                const int own1 = finC ? ax1 : ay1, pos1 = finC ? ay1 : ax1;
+                // alpha_{l0+len}(x_{l0+len}): final layout is C (lines = x) if len is odd
+                const bool finC = (len & 1) != 0;
+                const int xe0 = xp0[le];
+                const int xe1 = has1 ? int(xp1[le]) : xe0;
+                const int ex0 = xe0 % L, ey0 = xe0 / L, ex1 = xe1 % L, ey1 = xe1 / L;
+                const int own0 = finC ? ex0 : ey0, pos0 = finC ? ey0 : ex0;
+                const int own1 = finC ? ex1 : ey1, pos1 = finC ? ey1 : ex1;
                 if (active) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
@@ -340,12 +357,34 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             l = l1;
         }
         if (tid == 0) {
+            // log-weight of the block; with several blocks, the pair's last finished block
+            // sums the partials in block order (the same bits whichever finishes last)
             const double ln2 = 0.69314718055994530942;
-            st.logw[cd.logw_off + wl0] = double(esum0) * ln2 + log(double(fin0));
+            const double part0 = double(esum0) * ln2 + log(double(fin0));
+            const double part1 = double(esum1) * ln2 + log(double(fin1));
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
-            if (has1) {
-                st.logw[cd.logw_off + wl1] = double(esum1) * ln2 + log(double(fin1));
-                if (!(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
+            if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
+            double *lw = st.logw + cd.logw_off;
+            if (nblk == 1) {
+                lw[wl0] = part0;
+                if (has1) lw[wl1] = part1;
+            } else {
+                double *lp = st.logw_part + cd.lwp_off;
+                lp[wl0 * nblk + b] = part0;
+                if (has1) lp[wl1 * nblk + b] = part1;
+                __threadfence();
+                unsigned *done = st.blk_done + cd.done_off + rr;
+                if (atomicAdd(done, 1u) == unsigned(nblk - 1)) {
+                    __threadfence();
+                    double s0 = 0.0, s1 = 0.0;
+                    for (int k = 0; k < nblk; ++k) {
+                        s0 += __ldcg(lp + wl0 * nblk + k);
+                        if (has1) s1 += __ldcg(lp + wl1 * nblk + k);
+                    }
+                    lw[wl0] = s0;
+                    if (has1) lw[wl1] = s1;
+                    *done = 0u;  // ready for the next sweep
+                }
             }
         }
 
@@ -361,19 +400,20 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             cp_async_commit();
         };
         __syncthreads();
-        if (M > 1) prefetch(M - 1);
-        const float *hl = tb.h_f;
-        int cur0 = xa0, cur1 = xa1;
-        float ek0 = 0.f, ek1 = 0.f;
-        int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
+        if (len > 1) prefetch(len - 1);
+        const int xs0 = xp0[l0];
+        const int xs1 = has1 ? int(xp1[l0]) : xs0;
+        const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
+        int cur0 = xp0[le];
+        int cur1 = has1 ? int(xp1[le]) : cur0;
         if (tid == 0) {
-            atomicAdd(hist_s + (long long)a * N + xa0, 1);
-            if (has1) atomicAdd(hist_s + (long long)a * N + xa1, 1);
+            atomicAdd(hist_s + (long long)l0 * N + xs0, 1);
+            if (has1) atomicAdd(hist_s + (long long)l0 * N + xs1, 1);
         }
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
-        for (int i = M - 1; i >= 1; --i) {
-            int lb = a + i;
+        for (int i = len - 1; i >= 1; --i) {
+            int lb = l0 + i;
             if (lb >= M) lb -= M;
             cp_async_wait_all();
             __syncthreads();
@@ -513,8 +553,9 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             cur1 = nxt1;
         }
         if (tid == 0) {
-            ek0 += hl[(cur0 % L - ax0 + L) % L] + hl[(cur0 / L - ay0 + L) % L];
-            if (has1) ek1 += hl[(cur1 % L - ax1 + L) % L] + hl[(cur1 / L - ay1 + L) % L];
+            // link x_{l0} -> x_{l0+1}
+            ek0 += hl[(cur0 % L - sx0 + L) % L] + hl[(cur0 / L - sy0 + L) % L];
+            if (has1) ek1 += hl[(cur1 % L - sx1 + L) % L] + hl[(cur1 / L - sy1 + L) % L];
             atomicAdd(&st.meas[c].link_sum, double(ek0) + (has1 ? double(ek1) : 0.0));
         }
     }

@@ -40,6 +40,9 @@ struct ChainDev {
     double w_plus[2]; // W for s = +1, spin up / down: e^{+lambda}, e^{-lambda}
     double w_minus[2];
     double t, beta;
+    int block;          // FFBS block length B (0 or >= M: the closed loop from the anchor)
+    long long lwp_off;  // double offset of per-block log-weight partials [2 Nsig][nblk] (nblk > 1)
+    long long done_off; // unsigned offset of per-pair finished-block counters [2 npair] (nblk > 1)
     int gauss;          // 1: U < 0, continuous Gaussian field sigma, W = exp(gcoup sigma), both spins
     double gcoup;       // sqrt(|U| dtau)
     long long g_off;    // element offset of sigma [M][N] (doubles); W at 2 g_off: rows [M][L][L]
@@ -81,20 +84,30 @@ struct DevState {
     double *gsig;        // Gaussian fields sigma (U < 0 chains)
     void *gw;            // their slice potentials W = exp(a sigma), rows then columns
     int gw_f64;          // W stored as double (FP64 context) or float
+    double *logw_part;   // per-block log-weight partials of block FFBS
+    unsigned *blk_done;  // per-pair counters of finished blocks (zero between sweeps)
 };
+
+// Blocks of the FFBS loop of a chain: length B (0 or >= M: one block of M slices) and count.
+__host__ __device__ inline int ffbs_block_len(int block, int M) { return (block > 0 && block < M) ? block : M; }
+__host__ __device__ inline int ffbs_nblk(int block, int M) {
+    const int B = ffbs_block_len(block, M);
+    return (M + B - 1) / B;
+}
 
 enum : unsigned { kStatusDegenerate = 1u, kStatusNonPositive = 2u, kStatusTimeout = 4u };
 
-// One launch of the FFBS kernel covers the chains of one lattice size.
+// One launch of the FFBS kernel covers the chains of one lattice size.  Its work units are
+// (worldline pair, block) with the blocks of one pair independent given their held ends.
 struct FfbsLaunch {
     const int *class_chains;   // chain ids of this class
-    const int *class_pair_off; // [nclass + 1] prefix sums of 2*npair
+    const int *class_unit_off; // [nclass + 1] prefix sums of 2 npair nblk
     int nclass;
-    int total_pairs;
-    int M_max;                 // largest M in the class (scratch slot size)
-    void *scratch;             // slots of M_max * L * L complex values
+    int total_units;
+    int len_max;               // longest block in the class (scratch slot size, slices)
+    void *scratch;             // slots of len_max * L * L complex values
     long long slot_elems;      // complex elements per slot
-    unsigned *next_pair;       // work counter: groups take pairs in order (zeroed per launch)
+    unsigned *next_unit;       // work counter: groups take units in order (zeroed per launch)
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.

@@ -228,13 +228,13 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     ds.status = reinterpret_cast<unsigned *>(base + lay.status);
     FfbsLaunch fl{};
     fl.class_chains = reinterpret_cast<const int *>(base + lay.cls);
-    fl.class_pair_off = fl.class_chains + 1;
+    fl.class_unit_off = fl.class_chains + 1;  // the closed loop: one unit per pair
     fl.nclass = 1;
-    fl.total_pairs = int(total_pairs);
-    fl.M_max = M;
+    fl.total_units = int(total_pairs);
+    fl.len_max = M;
     fl.scratch = base + lay.slots;
     fl.slot_elems = (long long)M * L * L;
-    fl.next_pair = reinterpret_cast<unsigned *>(base + lay.cls) + 3;
+    fl.next_unit = reinterpret_cast<unsigned *>(base + lay.cls) + 3;
     e = f64 ? launch_ffbs_f64(L, ds, fl, int(grid), wpc, st) : launch_ffbs_f32(L, ds, fl, int(grid), wpc, st);
     if (e != cudaSuccess) return HQMC_ERR_CUDA;
     const long long nx = 2LL * Nsig * M;

@@ -48,15 +48,19 @@ struct HostChain {
     int L = 0, N = 0, M = 0, Nsig = 0;
     uint64_t seed = 0;
     double t = 0, U = 0, beta = 0, dtau = 0, filling = 0;
+    int block = 0;  // FFBS block length (0: the closed loop)
     bool set = false;
 };
 
 struct LClass {
     int L = 0;
     std::vector<int> chains;
-    std::vector<int> pair_off;  // prefix sums of 2*npair
+    std::vector<int> pair_off;  // prefix sums of 2*npair (the adjoint's work units)
+    std::vector<int> unit_off;  // prefix sums of 2*npair*nblk (FFBS work units: pair, block)
     int total_pairs = 0;
+    int total_units = 0;
     int M_max = 0;
+    int len_max = 0;            // longest FFBS block (scratch slot, slices)
     int grid = 0;          // CTAs launched
     long long groups = 0;  // worldline groups launched
     size_t scratch_off = 0;
@@ -305,10 +309,12 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         }
         it->chains.push_back(i);
     }
-    // within a size class the longest chains (largest M) go first: groups take pairs in
-    // this order from the class's work counter, which keeps the tail of a launch short
+    // within a size class the chains with the longest FFBS blocks (M, or B < M) go first:
+    // groups take work units in this order from the class's work counter, which keeps the
+    // tail of a launch short
+    auto blen = [&](int i) { return ffbs_block_len(c->ch[i].block, c->ch[i].M); };
     for (auto &k : c->classes)
-        std::stable_sort(k.chains.begin(), k.chains.end(), [&](int x, int y) { return c->ch[x].M > c->ch[y].M; });
+        std::stable_sort(k.chains.begin(), k.chains.end(), [&](int x, int y) { return blen(x) > blen(y); });
     size_t off = 0;
     auto take = [&](size_t b) {
         off = round_up(off, 256);
@@ -318,7 +324,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     };
     const size_t o_chains = take(sizeof(ChainDev) * nc);
     const size_t o_tabs = take(sizeof(ChainTab) * nc);
-    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0, gb = 0;
+    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0, gb = 0, pb = 0, db = 0;
     for (int i = 0; i < nc; ++i) {
         const HostChain &h = c->ch[i];
         ChainDev &d = c->cdev[i];
@@ -337,6 +343,14 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         d.t = h.t;
         d.beta = h.beta;
         d.gauss = h.U < 0.0 ? 1 : 0;
+        d.block = h.block;
+        const int nblk = ffbs_nblk(h.block, h.M);
+        d.lwp_off = pb;
+        d.done_off = db;
+        if (nblk > 1) {
+            pb += 2LL * h.Nsig * nblk;
+            db += 2LL * d.npair;
+        }
         d.gcoup = std::sqrt(std::fabs(h.U) * h.dtau);
         d.g_off = gb;
         if (d.gauss) gb += ((long long)h.M * h.N + 3) / 4 * 4;  // 16-byte aligned W lines
@@ -368,24 +382,33 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     const size_t o_stt = take(8);
     const size_t o_gs = take(size_t(gb) * 8);
     const size_t o_gw = take(size_t(gb) * 2 * (f64 ? 8 : 4));
+    const size_t o_lp = take(size_t(pb) * 8);
+    const size_t o_bd = take(size_t(db) * 4);
     c->off_cr = take(size_t(mb) * 8);
     c->off_sko = take(size_t(mb) * 8);
     // classes
     for (auto &k : c->classes) {
         k.pair_off.assign(1, 0);
+        k.unit_off.assign(1, 0);
         k.M_max = 0;
+        k.len_max = 0;
         for (int ci : k.chains) {
-            k.pair_off.push_back(k.pair_off.back() + 2 * c->cdev[ci].npair);
-            k.M_max = std::max(k.M_max, c->cdev[ci].M);
+            const ChainDev &d = c->cdev[ci];
+            k.pair_off.push_back(k.pair_off.back() + 2 * d.npair);
+            k.unit_off.push_back(k.unit_off.back() + 2 * d.npair * ffbs_nblk(d.block, d.M));
+            k.M_max = std::max(k.M_max, d.M);
+            k.len_max = std::max(k.len_max, ffbs_block_len(d.block, d.M));
         }
         k.total_pairs = k.pair_off.back();
-        k.cls_off = take(sizeof(int) * (k.chains.size() + k.pair_off.size() + 1));  // + work counter
+        k.total_units = k.unit_off.back();
+        // [chains][pair_off][work counter][unit_off]
+        k.cls_off = take(sizeof(int) * (k.chains.size() + k.pair_off.size() + 1 + k.unit_off.size()));
     }
     // FFBS grid and scratch per class
     for (auto &k : c->classes) {
         const int wpc = default_wpc(c, k.L);
         const int gpc = is_big(k.L) ? 1 : wpc * ffbs_groups_per_warp(k.L);  // wide lattices: one pair per CTA
-        const int need = (k.total_pairs + gpc - 1) / gpc;
+        const int need = (k.total_units + gpc - 1) / gpc;
         int grid = need;
         if (c->persistent) {
             int bps = 1;
@@ -399,7 +422,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         k.grid = std::max(1, grid);
         k.groups = (long long)k.grid * gpc;
         const size_t elem = f64 ? 16 : 8;
-        k.scratch_bytes = size_t(k.groups) * k.M_max * k.L * k.L * elem;
+        k.scratch_bytes = size_t(k.groups) * k.len_max * k.L * k.L * elem;
         k.scratch_off = take(k.scratch_bytes);
     }
     *total = round_up(off, 256);
@@ -420,6 +443,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     c->st.gsig = reinterpret_cast<double *>(o_gs);
     c->st.gw = reinterpret_cast<void *>(o_gw);
     c->st.gw_f64 = f64 ? 1 : 0;
+    c->st.logw_part = reinterpret_cast<double *>(o_lp);
+    c->st.blk_done = reinterpret_cast<unsigned *>(o_bd);
     return HQMC_OK;
 }
 
@@ -465,6 +490,8 @@ int prepare(hqmc_ctx *c) {
     s.status = rebase(s.status, c->base);
     s.gsig = rebase(s.gsig, c->base);
     s.gw = rebase(s.gw, c->base);
+    s.logw_part = rebase(s.logw_part, c->base);
+    s.blk_done = rebase(s.blk_done, c->base);
     c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
     c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
     cudaStream_t st = c->stream;
@@ -476,6 +503,8 @@ int prepare(hqmc_ctx *c) {
     for (auto &k : c->classes) {
         std::vector<int> buf(k.chains);
         buf.insert(buf.end(), k.pair_off.begin(), k.pair_off.end());
+        buf.push_back(0);  // work counter
+        buf.insert(buf.end(), k.unit_off.begin(), k.unit_off.end());
         HQMC_CUDA(c, cudaMemcpyAsync(c->base + k.cls_off, buf.data(), sizeof(int) * buf.size(), cudaMemcpyHostToDevice, st));
     }
     // kernel attributes are set here, outside any stream capture
@@ -566,16 +595,18 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     for (int k = 0; k < nk; ++k) {
         LClass &cl = c->classes[k];
         FfbsLaunch fl{};
-        fl.class_chains = reinterpret_cast<const int *>(c->base + cl.cls_off);
-        fl.class_pair_off = fl.class_chains + cl.chains.size();
-        fl.nclass = int(cl.chains.size());
-        fl.total_pairs = cl.total_pairs;
-        fl.M_max = cl.M_max;
+        int *cls = reinterpret_cast<int *>(c->base + cl.cls_off);
+        const size_t n = cl.chains.size();
+        fl.class_chains = cls;
+        fl.nclass = int(n);
+        fl.next_unit = reinterpret_cast<unsigned *>(cls + n + (n + 1));
+        fl.class_unit_off = cls + n + (n + 1) + 1;
+        fl.total_units = cl.total_units;
+        fl.len_max = cl.len_max;
         fl.scratch = c->base + cl.scratch_off;
-        fl.slot_elems = (long long)cl.M_max * cl.L * cl.L;
-        fl.next_pair = reinterpret_cast<unsigned *>(const_cast<int *>(fl.class_pair_off) + cl.pair_off.size());
+        fl.slot_elems = (long long)cl.len_max * cl.L * cl.L;
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
-        HQMC_CUDA(c, cudaMemsetAsync(fl.next_pair, 0, sizeof(unsigned), s));
+        HQMC_CUDA(c, cudaMemsetAsync(fl.next_unit, 0, sizeof(unsigned), s));
         const int wpc = default_wpc(c, cl.L);
         cudaError_t e = is_big(cl.L) ? launch_ffbs_big(cl.L, c->st, fl, cl.grid, s)
                         : f64        ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
@@ -743,6 +774,22 @@ int hqmc_set_params(hqmc_ctx *c, int chain, double t, double U, double beta, dou
     return HQMC_OK;
 }
 
+int hqmc_set_block(hqmc_ctx *c, int chain, int B) {
+    if (!c) return HQMC_ERR_ARG;
+    if (chain < -1 || chain >= c->nchains) return fail(c, HQMC_ERR_ARG, "chain index out of range");
+    if (B < 0) return fail(c, HQMC_ERR_ARG, "block length must be >= 0");
+    const int lo = chain < 0 ? 0 : chain, hi = chain < 0 ? c->nchains : chain + 1;
+    bool changed = false;
+    for (int i = lo; i < hi; ++i) {
+        changed = changed || c->ch[i].block != B;
+        c->ch[i].block = B;
+    }
+    // the work-unit tables, partial sums and scratch depend on the blocks: lay the context
+    // out again at its next use, keeping the state
+    if (changed) return stash_state(c);
+    return HQMC_OK;
+}
+
 int hqmc_set_stream(hqmc_ctx *c, void *stream) {
     if (!c) return HQMC_ERR_ARG;
     drop_graph(c);
@@ -827,6 +874,7 @@ int hqmc_autotune(hqmc_ctx *c, int trial_sweeps, int *n_tuned) {
         if (rc) return fail(c, rc, "autotune: temporary context");
         for (size_t i = 0; i < hs.size(); ++i) {
             rc = hqmc_set_params(t, int(i), hs[i]->t, hs[i]->U, hs[i]->beta, hs[i]->dtau, hs[i]->filling);
+            if (!rc) rc = hqmc_set_block(t, int(i), hs[i]->block);
             if (rc) break;
         }
         int best = 0;

@@ -24,6 +24,7 @@ _vp, _i, _d, _sz, _u64 = C.c_void_p, C.c_int, C.c_double, C.c_size_t, C.c_uint64
 SIGNATURES = {
     "hqmc_init_lattice": (_i, [C.POINTER(_vp), _i, _vp, _vp, _i, _i]),
     "hqmc_set_params": (_i, [_vp, _i, _d, _d, _d, _d, _d]),
+    "hqmc_set_block": (_i, [_vp, _i, _i]),
     "hqmc_set_stream": (_i, [_vp, _vp]),
     "hqmc_set_launch": (_i, [_vp, _i, _i, _i]),
     "hqmc_set_slice_launch": (_i, [_vp, _i]),
@@ -141,6 +142,13 @@ class Lattice:
         if chain == -1:
             self.params = (float(t), float(U), float(beta), float(dtau), float(filling))
         self.shapes = None
+
+    def set_block(self, B, chain=-1):
+        """FFBS block length (0 or >= M: the closed loop from the anchor; 1 <= B < M:
+        blocks from the anchor with both end sites held)."""
+        self._check(lib().hqmc_set_block(self._ctx, int(chain), int(B)))
+        if self.torch_memory and self._ws is not None:
+            self._attach()
 
     def set_checkpoint(self, stride=0, bf16=True):
         """Checkpoint stride of the adjoint's reverse pass (0 = ceil(sqrt M)) and format
