@@ -54,6 +54,14 @@ def lib():
         L.orc_sweep_gauss.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i, i]
         L.orc_sweep_gauss.restype = i
         L.orc_num_threads.restype = i
+        L.orc_local_step.argtypes = [i, i, i]
+        L.orc_local_step.restype = i
+        L.orc_local_ratio.argtypes = [i, i, vp, vp, i, i, i, i]
+        L.orc_local_ratio.restype = d
+        L.orc_local_color.argtypes = [i, i]
+        L.orc_local_color.restype = i
+        L.orc_sweep_local.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_sweep_local.restype = i
         _lib = L
     return _lib
 
@@ -158,6 +166,23 @@ class Chain:
             out["margin"] = margin
         return out
 
+    def local_sweep(self, want_margin=False):
+        """One local-update sweep (Eq. Rlocal in the position basis, then Gibbs); returns
+        a dict with hist, links, accepted (and margin)."""
+        M, N, Ns = self.M, self.N, self.Nsig
+        hist = np.zeros((2, M, N), dtype=np.int32)
+        margin = np.full((2, Ns, M), np.nan) if want_margin else None
+        links = np.full((2, Ns), np.nan)
+        acc = C.c_longlong(0)
+        lib().orc_sweep_local(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
+                              _p(self.s), _p(self.sigma), _p(self.x), _p(hist), _p(margin), _p(links),
+                              C.byref(acc))
+        self.sweep_count += 1
+        out = dict(hist=hist, links=links, accepted=acc.value)
+        if want_margin:
+            out["margin"] = margin
+        return out
+
     def grad(self, v=None):
         """(logZ, dlogZ/dv [2][M][N], dlogZ/dt) with every worldline anchored at slice 0."""
         dv = np.zeros((2, self.M, self.N))
@@ -200,6 +225,19 @@ def backward(L, M, g, f, a, seed, sweep, wl, xpath):
                        _p(np.ascontiguousarray(f, dtype=np.float64)), a, seed, sweep, wl,
                        _p(xp), _p(margin))
     return xp, margin
+
+
+def local_step(L, x, direction):
+    return lib().orc_local_step(L, x, direction)
+
+
+def local_ratio(L, M, g, Wl, xm, x, xn, xnew):
+    return lib().orc_local_ratio(L, M, _p(np.ascontiguousarray(g, dtype=np.float64)),
+                                 _p(np.ascontiguousarray(Wl, dtype=np.float64)), xm, x, xn, xnew)
+
+
+def local_color(M, l):
+    return lib().orc_local_color(M, l)
 
 
 def marginals(L, M, g, dg, v, x0):

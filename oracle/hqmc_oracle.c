@@ -28,6 +28,7 @@
  *                   phase 1: Gibbs draw, i = l, j = x
  *                   phase 2: anchor slice, i = 0, j = 0
  *                   phase 3: initial field, sweep = 2^64 - 1, i = l, j = x
+ *                   phase 4: local link update, i = sigma*Nsig + p, j = 2l (step), 2l+1 (accept)
  *
  * Every function that has no independent pin in tests/ says "parity unpinned" here;
  * at present every function is pinned (see tests/test_oracle_*.py).
@@ -292,6 +293,8 @@ void orc_backward(int L, int M, const double *g, const double *f_store, int a,
  * Worldlines are independent given s, so they are processed in parallel. */
 /* FFBS of every worldline (the first nwl of each spin) given the slice potentials
  * W [2][M][N] (spin-major): anchor, filter, backward draw, link sums. */
+static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp);
+
 static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
                         uint64_t seed, uint64_t sweep, int32_t *xpath, double *logw, double *margin,
                         double *links, int *anchor, int nwl, int block)
@@ -321,18 +324,23 @@ static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *d
             orc_backward_block(L, M, g, fst, l0, len, seed, sweep, wl, xp, margin ? margin + wl * M : NULL);
         }
         if (logw) logw[wl] = lz;
-        if (links) {
-            double acc = 0.0;
-            for (int l = 0; l < M; ++l) {
-                int x0 = xp[l], x1 = xp[(l + 1) % M];
-                int dx = orc_wrap((x1 % L) - (x0 % L), L), dy = orc_wrap((x1 / L) - (x0 / L), L);
-                acc += dg[dx] / g[dx] + dg[dy] / g[dy];
-            }
-            links[wl] = acc;
-        }
+        if (links) links[wl] = orc_link_sum(L, M, g, dg, xp);
         free(fst);
     }
     return a;
+}
+
+/* Kinetic estimator of one closed worldline: sum over its M links of
+ * d/dt log G(x_{l+1} - x_l) = g'(dx)/g(dx) + g'(dy)/g(dy). */
+static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp)
+{
+    double acc = 0.0;
+    for (int l = 0; l < M; ++l) {
+        int x0 = xp[l], x1 = xp[(l + 1) % M];
+        int dx = orc_wrap((x1 % L) - (x0 % L), L), dy = orc_wrap((x1 / L) - (x0 / L), L);
+        acc += dg[dx] / g[dx] + dg[dy] / g[dy];
+    }
+    return acc;
 }
 
 /* Occupancy histogram [2][M][N] of the current worldlines. */
@@ -346,6 +354,34 @@ static void orc_histogram(int L, int M, int Nsig, const int32_t *xpath, int32_t 
                 n[((size_t)sg * M + l) * N + xpath[((size_t)sg * Nsig + p) * M + l]] += 1;
 }
 
+/* Hirsch-Gibbs step (Sec. 3.5.4): every field from its factorised conditional
+ * P(s = +1 | paths) = 1 / (1 + exp(-2 lambda m)), m = n_up - n_dn, phase-1 uniform. */
+static void orc_gibbs_hirsch(int L, int M, double lam, uint64_t seed, uint64_t sweep, const int32_t *n, int8_t *s)
+{
+    int N = L * L;
+    for (int l = 0; l < M; ++l)
+        for (int x = 0; x < N; ++x) {
+            int m = n[(size_t)l * N + x] - n[((size_t)M + l) * N + x];
+            double pplus = 1.0 / (1.0 + exp(-2.0 * lam * m));
+            double u = orc_uniform(seed, sweep, 1, (uint64_t)l, (uint64_t)x);
+            s[(size_t)l * N + x] = (u < pplus) ? 1 : -1;
+        }
+}
+
+/* Hirsch slice potentials W [2][M][N] = exp(sigma lambda s), sigma = +1 up, -1 down. */
+static double *orc_hirsch_W(int L, int M, double lam, const int8_t *s)
+{
+    int N = L * L;
+    double *W = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg) {
+        double sigma = sg == 0 ? 1.0 : -1.0;
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x)
+                W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
+    }
+    return W;
+}
+
 int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
               int8_t *s, int32_t *xpath, double *logw, int32_t *hist, double *margin,
               double *links, int *anchor, int nwl_limit, int block)
@@ -354,25 +390,13 @@ int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t 
     double lam = orc_lambda(U, dtau);
     double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
     orc_g_table(L, t, dtau, g, dg);
-    double *W = malloc((size_t)2 * M * N * sizeof(double));
-    for (int sg = 0; sg < 2; ++sg) {
-        double sigma = sg == 0 ? 1.0 : -1.0;
-        for (int l = 0; l < M; ++l)
-            for (int x = 0; x < N; ++x)
-                W[((size_t)sg * M + l) * N + x] = exp(sigma * lam * s[(size_t)l * N + x]);
-    }
+    double *W = orc_hirsch_W(L, M, lam, s);
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
     orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);
-        for (int l = 0; l < M; ++l)
-            for (int x = 0; x < N; ++x) {
-                int m = n[(size_t)l * N + x] - n[((size_t)M + l) * N + x];
-                double pplus = 1.0 / (1.0 + exp(-2.0 * lam * m));
-                double u = orc_uniform(seed, sweep, 1, (uint64_t)l, (uint64_t)x);
-                s[(size_t)l * N + x] = (u < pplus) ? 1 : -1;
-            }
+        orc_gibbs_hirsch(L, M, lam, seed, sweep, n, s);
         if (!hist) free(n);
     }
     free(g); free(dg); free(W);
@@ -411,6 +435,32 @@ void orc_init_sigma(int L, int M, uint64_t seed, double *sigma)
                                                   orc_uniform(seed, UINT64_MAX, 3, (uint64_t)l, 2 * (uint64_t)x + 1));
 }
 
+/* Gaussian Gibbs step (Eq. gaussCond): sigma_{x,l} ~ N(a (n_up + n_dn - 1/2), 1), the
+ * normal from the phase-1 uniforms of j = 2x, 2x+1. */
+static void orc_gibbs_gauss(int L, int M, double a, uint64_t seed, uint64_t sweep, const int32_t *n, double *sigma)
+{
+    int N = L * L;
+    for (int l = 0; l < M; ++l)
+        for (int x = 0; x < N; ++x) {
+            int nt = n[(size_t)l * N + x] + n[((size_t)M + l) * N + x];
+            double u1 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x);
+            double u2 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x + 1);
+            sigma[(size_t)l * N + x] = a * (nt - 0.5) + orc_normal(u1, u2);
+        }
+}
+
+/* Gaussian-field slice potentials W [2][M][N] = exp(a sigma), both spins. */
+static double *orc_gauss_W(int L, int M, double a, const double *sigma)
+{
+    int N = L * L;
+    double *W = malloc((size_t)2 * M * N * sizeof(double));
+    for (int sg = 0; sg < 2; ++sg)
+        for (int l = 0; l < M; ++l)
+            for (int x = 0; x < N; ++x)
+                W[((size_t)sg * M + l) * N + x] = exp(a * sigma[(size_t)l * N + x]);
+    return W;
+}
+
 /* One sweep with the Gaussian field: FFBS as in orc_sweep with W = exp(a sigma) for both
  * spins, then sigma_{x,l} ~ N(a (n_up + n_dn - 1/2), 1), drawn from phase 1 with
  * j = 2x, 2x+1. */
@@ -422,25 +472,114 @@ int orc_sweep_gauss(int L, int M, int Nsig, double t, double U, double dtau, uin
     double a = orc_gauss_coupling(U, dtau);
     double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
     orc_g_table(L, t, dtau, g, dg);
-    double *W = malloc((size_t)2 * M * N * sizeof(double));
-    for (int sg = 0; sg < 2; ++sg)
-        for (int l = 0; l < M; ++l)
-            for (int x = 0; x < N; ++x)
-                W[((size_t)sg * M + l) * N + x] = exp(a * sigma[(size_t)l * N + x]);
+    double *W = orc_gauss_W(L, M, a, sigma);
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
     orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);
-        for (int l = 0; l < M; ++l)
-            for (int x = 0; x < N; ++x) {
-                int nt = n[(size_t)l * N + x] + n[((size_t)M + l) * N + x];
-                double u1 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x);
-                double u2 = orc_uniform(seed, sweep, 1, (uint64_t)l, 2 * (uint64_t)x + 1);
-                sigma[(size_t)l * N + x] = a * (nt - 0.5) + orc_normal(u1, u2);
-            }
+        orc_gibbs_gauss(L, M, a, seed, sweep, n, sigma);
         if (!hist) free(n);
     }
+    free(g); free(dg); free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Local link update (Sec. 3.5.1, Eq. Rlocal), read in the position basis: the */
+/* momentum-space ratio's kinetic factors become the propagators G to the two  */
+/* held neighbours and its potential factors become W_l at the old and new     */
+/* site.  One site x_l of one worldline moves by one lattice step e (uniform   */
+/* over +x, -x, +y, -y, a symmetric proposal) with x_{l-1}, x_{l+1} held, and  */
+/* is accepted with probability min(1, R) (Metropolis).                        */
+/* ------------------------------------------------------------------------- */
+
+/* The site one lattice step from x: dir 0 = +x, 1 = -x, 2 = +y, 3 = -y. */
+int orc_local_step(int L, int x, int dir)
+{
+    int ix = x % L, iy = x / L;
+    if (dir == 0) ix = orc_wrap(ix + 1, L);
+    else if (dir == 1) ix = orc_wrap(ix - 1, L);
+    else if (dir == 2) iy = orc_wrap(iy + 1, L);
+    else iy = orc_wrap(iy - 1, L);
+    return ix + L * iy;
+}
+
+/* R of moving slice l of a worldline from x to xnew, given the slice potential Wl [N] and
+ * the held neighbours xm = x_{l-1}, xn = x_{l+1}:
+ *   R = G(xnew - xm) W_l(xnew) G(xn - xnew) / (G(x - xm) W_l(x) G(xn - x)).
+ * M = 1 (the slice is its own neighbour, the link G(0) does not change): R = W(xnew)/W(x). */
+double orc_local_ratio(int L, int M, const double *g, const double *Wl, int xm, int x, int xn, int xnew)
+{
+    if (M == 1) return Wl[xnew] / Wl[x];
+    double num = orc_G(g, L, xm, xnew) * Wl[xnew] * orc_G(g, L, xnew, xn);
+    double den = orc_G(g, L, xm, x) * Wl[x] * orc_G(g, L, x, xn);
+    return num / den;
+}
+
+/* Colour of slice l: slices of one colour are never neighbours in imaginary time, so
+ * their updates are independent given the rest (even l, odd l, and l = M-1 alone when
+ * M is odd). */
+int orc_local_color(int M, int l)
+{
+    return (M % 2 == 1 && l == M - 1) ? 2 : l % 2;
+}
+
+/* One local sweep of every worldline given W [2][M][N]: colours 0, 1, 2 in turn, every
+ * slice of the colour proposed once.  Uniforms: phase 4, i = sigma Nsig + p, j = 2l for
+ * the step (dir = floor(4u)) and j = 2l + 1 for the acceptance (accept iff u < R).
+ * margin[wl][l] (optional) receives |u - R| (INFINITY when R >= 1: always accepted).
+ * Returns the number of accepted moves. */
+static long long orc_local_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
+                               uint64_t seed, uint64_t sweep, int32_t *xpath, double *margin, double *links)
+{
+    int N = L * L;
+    long long accepted = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : accepted) if (2 * Nsig >= 2 * orc_num_threads())
+    for (int k = 0; k < 2 * Nsig; ++k) {
+        int sg = k / Nsig;
+        uint64_t wl = (uint64_t)k;
+        int32_t *xp = xpath + wl * M;
+        for (int c = 0; c < 3; ++c)
+            for (int l = 0; l < M; ++l) {
+                if (orc_local_color(M, l) != c) continue;
+                int xm = xp[(l + M - 1) % M], x = xp[l], xn = xp[(l + 1) % M];
+                double u0 = orc_uniform(seed, sweep, 4, wl, 2 * (uint64_t)l);
+                double u1 = orc_uniform(seed, sweep, 4, wl, 2 * (uint64_t)l + 1);
+                int dir = (int)(u0 * 4.0);
+                if (dir > 3) dir = 3;
+                int xnew = orc_local_step(L, x, dir);
+                double R = orc_local_ratio(L, M, g, W + ((size_t)sg * M + l) * N, xm, x, xn, xnew);
+                if (margin) margin[wl * M + l] = (R >= 1.0) ? INFINITY : fabs(u1 - R);
+                if (u1 < R) {
+                    xp[l] = xnew;
+                    ++accepted;
+                }
+            }
+        if (links) links[wl] = orc_link_sum(L, M, g, dg, xp);
+    }
+    return accepted;
+}
+
+/* One local-update sweep of one chain: local moves of every worldline (above), occupancy,
+ * then the same Gibbs step as the FFBS sweep (Hirsch for U >= 0 with s; Gaussian for
+ * U < 0 with sigma).  Outputs as in orc_sweep; *accepted receives the accepted moves. */
+int orc_sweep_local(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
+                    int8_t *s, double *sigma, int32_t *xpath, int32_t *hist, double *margin, double *links,
+                    long long *accepted)
+{
+    int N = L * L;
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    double lam = U < 0.0 ? 0.0 : orc_lambda(U, dtau), a = orc_gauss_coupling(U, dtau);
+    double *W = U < 0.0 ? orc_gauss_W(L, M, a, sigma) : orc_hirsch_W(L, M, lam, s);
+    long long acc = orc_local_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, margin, links);
+    if (accepted) *accepted = acc;
+    int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
+    orc_histogram(L, M, Nsig, xpath, n);
+    if (U < 0.0) orc_gibbs_gauss(L, M, a, seed, sweep, n, sigma);
+    else orc_gibbs_hirsch(L, M, lam, seed, sweep, n, s);
+    if (!hist) free(n);
     free(g); free(dg); free(W);
     return 0;
 }
