@@ -60,8 +60,12 @@ def lib():
         L.orc_local_ratio.restype = d
         L.orc_local_color.argtypes = [i, i]
         L.orc_local_color.restype = i
-        L.orc_sweep_local.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_sweep_local.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_sweep_local.restype = i
+        L.orc_perm_ratio.argtypes = [i, vp, i, i, i, i]
+        L.orc_perm_ratio.restype = d
+        L.orc_sweep_perm.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
+        L.orc_sweep_perm.restype = i
         _lib = L
     return _lib
 
@@ -135,6 +139,9 @@ class Chain:
         self.s = np.zeros((self.M, self.N), dtype=np.int8)
         self.x = np.zeros((2, self.Nsig, self.M), dtype=np.int32)
         lib().orc_init_state(L, self.M, self.Nsig, seed, _p(self.s), _p(self.x))
+        # permutation at tau = beta (identity: every worldline closes on itself) and its sign
+        self.perm = np.tile(np.arange(self.Nsig, dtype=np.int32), (2, 1))
+        self.sign = 1
         self.sigma = None
         if self.gauss:
             self.sigma = np.zeros((self.M, self.N))
@@ -176,11 +183,35 @@ class Chain:
         acc = C.c_longlong(0)
         lib().orc_sweep_local(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
                               _p(self.s), _p(self.sigma), _p(self.x), _p(hist), _p(margin), _p(links),
-                              C.byref(acc))
+                              C.byref(acc), _p(self.perm))
         self.sweep_count += 1
         out = dict(hist=hist, links=links, accepted=acc.value)
         if want_margin:
             out["margin"] = margin
+        return out
+
+    def perm_sweep(self, want_margin=False, block=0):
+        """One sweep with permutations: pair-swap update at tau = beta, FFBS of every
+        worldline's unit under the new permutation, Gibbs.  Returns a dict with logw (per
+        unit), hist, anchor, links, swaps, sign (and margin, margin_perm)."""
+        M, N, Ns = self.M, self.N, self.Nsig
+        logw = np.full((2, Ns), np.nan)
+        hist = np.zeros((2, M, N), dtype=np.int32)
+        margin = np.full((2, Ns, M), np.nan) if want_margin else None
+        mperm = np.full((2, max(1, Ns // 2)), np.nan) if want_margin else None
+        links = np.full((2, Ns), np.nan)
+        anchor = C.c_int(-1)
+        sign = C.c_int(self.sign)
+        swaps = C.c_longlong(0)
+        lib().orc_sweep_perm(self.L, M, Ns, self.t, self.U, self.dtau, self.seed, self.sweep_count,
+                             _p(self.s), _p(self.sigma), _p(self.x), _p(self.perm), C.byref(sign), _p(logw),
+                             _p(hist), _p(margin), _p(mperm), _p(links), C.byref(anchor), block, C.byref(swaps))
+        self.sign = sign.value
+        self.sweep_count += 1
+        out = dict(logw=logw, hist=hist, anchor=anchor.value, links=links, swaps=swaps.value, sign=self.sign)
+        if want_margin:
+            out["margin"] = margin
+            out["margin_perm"] = mperm
         return out
 
     def grad(self, v=None):
@@ -225,6 +256,10 @@ def backward(L, M, g, f, a, seed, sweep, wl, xpath):
                        _p(np.ascontiguousarray(f, dtype=np.float64)), a, seed, sweep, wl,
                        _p(xp), _p(margin))
     return xp, margin
+
+
+def perm_ratio(L, g, xlp, xlq, a0, b0):
+    return lib().orc_perm_ratio(L, _p(np.ascontiguousarray(g, dtype=np.float64)), xlp, xlq, a0, b0)
 
 
 def local_step(L, x, direction):

@@ -29,6 +29,11 @@
  *                   phase 2: anchor slice, i = 0, j = 0
  *                   phase 3: initial field, sweep = 2^64 - 1, i = l, j = x
  *                   phase 4: local link update, i = sigma*Nsig + p, j = 2l (step), 2l+1 (accept)
+ *                   phase 5: permutation update, i = sigma, j = 0 (pairing), 1 + k (pair k)
+ *   permutations    perm[sigma][p] = P(p): worldline p's slice M-1 links to slice 0 of
+ *                   worldline P(p) (x_M^{(p)} = x_0^{(P(p))}, Sec. 3.5.3); the identity
+ *                   closes every worldline on itself.  The sampled weight is |w|; the
+ *                   sign sgn(P_up) sgn(P_dn) reweights observables (Eq. reweight).
  *
  * Every function that has no independent pin in tests/ says "parity unpinned" here;
  * at present every function is pinned (see tests/test_oracle_*.py).
@@ -293,11 +298,17 @@ void orc_backward(int L, int M, const double *g, const double *f_store, int a,
  * Worldlines are independent given s, so they are processed in parallel. */
 /* FFBS of every worldline (the first nwl of each spin) given the slice potentials
  * W [2][M][N] (spin-major): anchor, filter, backward draw, link sums. */
-static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp);
+static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp, int next0);
 
+/* perm (nullable: the identity) [2][Nsig]: with a permutation, the unit of worldline p is
+ * the stretch from slice a of p to slice a of P(p): slices a+1..M-1 of p, then 0..a-1 of
+ * P(p), with the ends x_a^{(p)} and x_a^{(P(p))} held (with P = identity, the closed loop
+ * of p).  The units partition every slice but a, so they are independent given the slice-a
+ * sites.  Unit p draws with the uniforms of worldline p.  margin and the drawn sites go to
+ * the owning worldline. */
 static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
                         uint64_t seed, uint64_t sweep, int32_t *xpath, double *logw, double *margin,
-                        double *links, int *anchor, int nwl, int block)
+                        double *links, int *anchor, int nwl, int block, const int32_t *perm)
 {
     int B = (block > 0 && block < M) ? block : M;
     int nblk = (M + B - 1) / B;
@@ -312,31 +323,56 @@ static int orc_ffbs_all(int L, int M, int Nsig, const double *g, const double *d
     for (int k = 0; k < total; ++k) {
         int sg = k / nwl, p = k % nwl;
         uint64_t wl = (uint64_t)sg * Nsig + p;
-        int32_t *xp = xpath + wl * M;
+        uint64_t wq = (uint64_t)sg * Nsig + (perm ? perm[wl] : p);
+        int32_t *xp = xpath + wl * M, *xq = xpath + wq * M;
         double *fst = malloc((size_t)M * N * sizeof(double));
+        /* the unit's sites by slice: p from a on, P(p) before a; at a itself the end site
+         * x_a^{(P(p))}, which the last interior draw conditions on */
+        int32_t *vp = malloc(M * sizeof(int32_t));
+        double *vm = margin ? malloc(M * sizeof(double)) : NULL;
+        for (int l = 0; l < M; ++l) vp[l] = (l < a) ? xq[l] : xp[l];
+        vp[a] = xq[a];
         /* blocks a, a+B, a+2B, ... (the last one may be shorter), resampled in turn with
          * their end sites held; the log-weight is the sum of the blocks' */
         double lz = 0.0;
         for (int b = 0; b < nblk; ++b) {
             int l0 = (a + b * B) % M, len = (b + 1) * B <= M ? B : M - b * B;
-            int xs = xp[l0], xe = xp[(l0 + len) % M];
+            int xs = (b == 0) ? xp[a] : vp[l0], xe = vp[(l0 + len) % M];
             lz += orc_filter_block(L, M, g, W + (size_t)sg * M * N, l0, len, xs, xe, fst);
-            orc_backward_block(L, M, g, fst, l0, len, seed, sweep, wl, xp, margin ? margin + wl * M : NULL);
+            orc_backward_block(L, M, g, fst, l0, len, seed, sweep, wl, vp, vm);
         }
+        for (int l = 0; l < M; ++l) {
+            if (l == a) continue;
+            if (l < a) xq[l] = vp[l];
+            else xp[l] = vp[l];
+            if (vm) margin[((l < a) ? wq : wl) * M + l] = vm[l];
+        }
+        if (vm) margin[wl * M + a] = INFINITY; /* slice a is held */
         if (logw) logw[wl] = lz;
-        if (links) links[wl] = orc_link_sum(L, M, g, dg, xp);
         free(fst);
+        free(vp);
+        free(vm);
     }
+    /* link sums of the final paths (a second pass: a worldline's early slices belong to
+     * another unit) */
+    if (links)
+        for (int k = 0; k < total; ++k) {
+            int sg = k / nwl, p = k % nwl;
+            uint64_t wl = (uint64_t)sg * Nsig + p;
+            uint64_t wq = (uint64_t)sg * Nsig + (perm ? perm[wl] : p);
+            links[wl] = orc_link_sum(L, M, g, dg, xpath + wl * M, xpath[wq * M]);
+        }
     return a;
 }
 
-/* Kinetic estimator of one closed worldline: sum over its M links of
- * d/dt log G(x_{l+1} - x_l) = g'(dx)/g(dx) + g'(dy)/g(dy). */
-static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp)
+/* Kinetic estimator of one worldline: sum over its M links of
+ * d/dt log G(x_{l+1} - x_l) = g'(dx)/g(dx) + g'(dy)/g(dy), the last link going to next0
+ * (its own x_0 when closed on itself, x_0 of P(p) with a permutation). */
+static double orc_link_sum(int L, int M, const double *g, const double *dg, const int32_t *xp, int next0)
 {
     double acc = 0.0;
     for (int l = 0; l < M; ++l) {
-        int x0 = xp[l], x1 = xp[(l + 1) % M];
+        int x0 = xp[l], x1 = (l + 1 < M) ? xp[l + 1] : next0;
         int dx = orc_wrap((x1 % L) - (x0 % L), L), dy = orc_wrap((x1 / L) - (x0 / L), L);
         acc += dg[dx] / g[dx] + dg[dy] / g[dy];
     }
@@ -392,7 +428,7 @@ int orc_sweep(int L, int M, int Nsig, double t, double U, double dtau, uint64_t 
     orc_g_table(L, t, dtau, g, dg);
     double *W = orc_hirsch_W(L, M, lam, s);
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
-    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block, NULL);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);
@@ -474,7 +510,7 @@ int orc_sweep_gauss(int L, int M, int Nsig, double t, double U, double dtau, uin
     orc_g_table(L, t, dtau, g, dg);
     double *W = orc_gauss_W(L, M, a, sigma);
     int nwl = (nwl_limit >= 0 && nwl_limit < Nsig) ? nwl_limit : Nsig;
-    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block);
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, nwl, block, NULL);
     if (nwl_limit < 0 || nwl_limit >= Nsig) {
         int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
         orc_histogram(L, M, Nsig, xpath, n);
@@ -526,24 +562,34 @@ int orc_local_color(int M, int l)
 }
 
 /* One local sweep of every worldline given W [2][M][N]: colours 0, 1, 2 in turn, every
- * slice of the colour proposed once.  Uniforms: phase 4, i = sigma Nsig + p, j = 2l for
- * the step (dir = floor(4u)) and j = 2l + 1 for the acceptance (accept iff u < R).
- * margin[wl][l] (optional) receives |u - R| (INFINITY when R >= 1: always accepted).
- * Returns the number of accepted moves. */
+ * slice of the colour of every worldline proposed once.  With a permutation perm
+ * (nullable: the identity), slice 0 of p follows slice M-1 of P^{-1}(p) and slice M-1 of p
+ * precedes slice 0 of P(p); those are of other colours (M >= 2), so one colour's moves stay
+ * independent.  Uniforms: phase 4, i = sigma Nsig + p, j = 2l for the step
+ * (dir = floor(4u)) and j = 2l + 1 for the acceptance (accept iff u < R).  margin[wl][l]
+ * (optional) receives |u - R| (INFINITY when R >= 1: always accepted).  Returns the
+ * number of accepted moves. */
 static long long orc_local_all(int L, int M, int Nsig, const double *g, const double *dg, const double *W,
-                               uint64_t seed, uint64_t sweep, int32_t *xpath, double *margin, double *links)
+                               uint64_t seed, uint64_t sweep, int32_t *xpath, double *margin, double *links,
+                               const int32_t *perm)
 {
     int N = L * L;
     long long accepted = 0;
+    int32_t *pinv = malloc((size_t)2 * Nsig * sizeof(int32_t));
+    for (int k = 0; k < 2 * Nsig; ++k) pinv[k] = k % Nsig;
+    if (perm)
+        for (int k = 0; k < 2 * Nsig; ++k) pinv[(k / Nsig) * Nsig + perm[k]] = k % Nsig;
+    for (int c = 0; c < 3; ++c) {
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : accepted) if (2 * Nsig >= 2 * orc_num_threads())
-    for (int k = 0; k < 2 * Nsig; ++k) {
-        int sg = k / Nsig;
-        uint64_t wl = (uint64_t)k;
-        int32_t *xp = xpath + wl * M;
-        for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 2 * Nsig; ++k) {
+            int sg = k / Nsig;
+            uint64_t wl = (uint64_t)k;
+            int32_t *xp = xpath + wl * M;
+            const int32_t *xprev = xpath + ((uint64_t)sg * Nsig + pinv[k]) * M;
+            const int32_t *xnext = xpath + ((uint64_t)sg * Nsig + (perm ? perm[k] : k % Nsig)) * M;
             for (int l = 0; l < M; ++l) {
                 if (orc_local_color(M, l) != c) continue;
-                int xm = xp[(l + M - 1) % M], x = xp[l], xn = xp[(l + 1) % M];
+                int xm = (l > 0) ? xp[l - 1] : xprev[M - 1], x = xp[l], xn = (l + 1 < M) ? xp[l + 1] : xnext[0];
                 double u0 = orc_uniform(seed, sweep, 4, wl, 2 * (uint64_t)l);
                 double u1 = orc_uniform(seed, sweep, 4, wl, 2 * (uint64_t)l + 1);
                 int dir = (int)(u0 * 4.0);
@@ -556,8 +602,14 @@ static long long orc_local_all(int L, int M, int Nsig, const double *g, const do
                     ++accepted;
                 }
             }
-        if (links) links[wl] = orc_link_sum(L, M, g, dg, xp);
+        }
     }
+    if (links)
+        for (int k = 0; k < 2 * Nsig; ++k) {
+            uint64_t wq = (uint64_t)(k / Nsig) * Nsig + (perm ? perm[k] : k % Nsig);
+            links[k] = orc_link_sum(L, M, g, dg, xpath + (uint64_t)k * M, xpath[wq * M]);
+        }
+    free(pinv);
     return accepted;
 }
 
@@ -566,15 +618,94 @@ static long long orc_local_all(int L, int M, int Nsig, const double *g, const do
  * U < 0 with sigma).  Outputs as in orc_sweep; *accepted receives the accepted moves. */
 int orc_sweep_local(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
                     int8_t *s, double *sigma, int32_t *xpath, int32_t *hist, double *margin, double *links,
-                    long long *accepted)
+                    long long *accepted, const int32_t *perm)
 {
     int N = L * L;
     double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
     orc_g_table(L, t, dtau, g, dg);
     double lam = U < 0.0 ? 0.0 : orc_lambda(U, dtau), a = orc_gauss_coupling(U, dtau);
     double *W = U < 0.0 ? orc_gauss_W(L, M, a, sigma) : orc_hirsch_W(L, M, lam, s);
-    long long acc = orc_local_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, margin, links);
+    long long acc = orc_local_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, margin, links, perm);
     if (accepted) *accepted = acc;
+    int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
+    orc_histogram(L, M, Nsig, xpath, n);
+    if (U < 0.0) orc_gibbs_gauss(L, M, a, seed, sweep, n, sigma);
+    else orc_gibbs_hirsch(L, M, lam, seed, sweep, n, s);
+    if (!hist) free(n);
+    free(g); free(dg); free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Permutation updates (Sec. 3.5.3): reconnect worldlines at tau = beta.  A   */
+/* pair swap exchanges the successors of two worldlines p, q of one spin,      */
+/* P'(p) = P(q), P'(q) = P(p); only the two links across tau = beta change.   */
+/* Sampling |w|, it is accepted with probability min(1, R); each accepted swap */
+/* flips sgn(P), which reweights observables (Eq. reweight).                  */
+/* ------------------------------------------------------------------------- */
+
+/* R of the swap, from the last sites xlp = x_{M-1}^{(p)}, xlq = x_{M-1}^{(q)} and the
+ * successors' first sites a0 = x_0^{(P(p))}, b0 = x_0^{(P(q))}:
+ *   R = G(b0 - xlp) G(a0 - xlq) / (G(a0 - xlp) G(b0 - xlq)). */
+double orc_perm_ratio(int L, const double *g, int xlp, int xlq, int a0, int b0)
+{
+    return (orc_G(g, L, xlp, b0) * orc_G(g, L, xlq, a0)) / (orc_G(g, L, xlp, a0) * orc_G(g, L, xlq, b0));
+}
+
+/* One permutation update of both spins.  Pairing: rotation r = floor(u Nsig) (phase 5,
+ * i = sigma, j = 0) and the disjoint pairs (2k + r, 2k + 1 + r) mod Nsig, k < Nsig/2 (a
+ * state-independent choice, each swap its own inverse, so the proposal is symmetric;
+ * over the rotations every adjacent transposition is proposed, which generates every
+ * permutation).  Pair k is accepted iff u < R (phase 5, i = sigma, j = 1 + k).
+ * margin (optional) [2][Nsig/2] receives |u - R| (INFINITY when R >= 1).  Returns the
+ * accepted swaps; *sign flips with each. */
+static long long orc_perm_update(int L, int M, int Nsig, const double *g, uint64_t seed, uint64_t sweep,
+                                 const int32_t *xpath, int32_t *perm, int *sign, double *margin)
+{
+    long long acc = 0;
+    int npr = Nsig / 2;
+    for (int sg = 0; sg < 2; ++sg) {
+        if (npr == 0) continue;
+        int r = (int)floor(orc_uniform(seed, sweep, 5, (uint64_t)sg, 0) * Nsig);
+        if (r >= Nsig) r = Nsig - 1;
+        int32_t *P = perm + (size_t)sg * Nsig;
+        const int32_t *X = xpath + (size_t)sg * Nsig * M;
+        for (int k = 0; k < npr; ++k) {
+            int p = (2 * k + r) % Nsig, q = (2 * k + 1 + r) % Nsig;
+            double R = orc_perm_ratio(L, g, X[(size_t)p * M + M - 1], X[(size_t)q * M + M - 1],
+                                      X[(size_t)P[p] * M], X[(size_t)P[q] * M]);
+            double u = orc_uniform(seed, sweep, 5, (uint64_t)sg, 1 + (uint64_t)k);
+            if (margin) margin[(size_t)sg * npr + k] = (R >= 1.0) ? INFINITY : fabs(u - R);
+            if (u < R) {
+                int t = P[p];
+                P[p] = P[q];
+                P[q] = t;
+                *sign = -*sign;
+                ++acc;
+            }
+        }
+    }
+    return acc;
+}
+
+/* One sweep with permutations: the permutation update (above), then FFBS of every
+ * worldline's unit under the new permutation (orc_ffbs_all), the occupancy and the Gibbs
+ * step of the chain's field type.  perm [2][Nsig] and *sign are updated in place;
+ * *swaps receives the accepted swaps; margin_perm [2][Nsig/2] (nullable).  Other outputs
+ * as in orc_sweep (logw per unit). */
+int orc_sweep_perm(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed, uint64_t sweep,
+                   int8_t *s, double *sigma, int32_t *xpath, int32_t *perm, int *sign, double *logw,
+                   int32_t *hist, double *margin, double *margin_perm, double *links, int *anchor, int block,
+                   long long *swaps)
+{
+    int N = L * L;
+    double *g = malloc(L * sizeof(double)), *dg = malloc(L * sizeof(double));
+    orc_g_table(L, t, dtau, g, dg);
+    double lam = U < 0.0 ? 0.0 : orc_lambda(U, dtau), a = orc_gauss_coupling(U, dtau);
+    double *W = U < 0.0 ? orc_gauss_W(L, M, a, sigma) : orc_hirsch_W(L, M, lam, s);
+    long long acc = orc_perm_update(L, M, Nsig, g, seed, sweep, xpath, perm, sign, margin_perm);
+    if (swaps) *swaps = acc;
+    orc_ffbs_all(L, M, Nsig, g, dg, W, seed, sweep, xpath, logw, margin, links, anchor, Nsig, block, perm);
     int32_t *n = hist ? hist : malloc((size_t)2 * M * N * sizeof(int32_t));
     orc_histogram(L, M, Nsig, xpath, n);
     if (U < 0.0) orc_gibbs_gauss(L, M, a, seed, sweep, n, sigma);
