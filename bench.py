@@ -267,6 +267,8 @@ def main():
     ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS) + ["grad16"],
                     help="L32 (default, the headline configuration), ragged, L64, L128, paper8/16/32 "
                          "(M=1024); grad16 times the adjoint")
+    ap.add_argument("--local-steps", type=int, default=20,
+                    help="local-update sweeps timed beside the FFBS sweep (0: skip)")
     ap.add_argument("--block", type=int, default=0,
                     help="FFBS block length B (0: the closed loop from the anchor, the default)")
     ap.add_argument("--beta", type=float, default=None,
@@ -398,6 +400,23 @@ def main():
     e2e_val = max_over_ranks(te)
     e2e = {"value": world * ke / e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": int(8 * sum(2 * ns for (_, _, ns) in shapes)) + 4}
+    # local link updates (Eq. Rlocal in the position basis) on the same chains: one
+    # launch per slice colour, then the same Gibbs/measure step; plain launches
+    local_upd = None
+    if args.local_steps > 0:
+        lat.measure(reset=True)
+        lat.local_sweep(3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.local_sweep(args.local_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loc = max_over_ranks(e0.elapsed_time(e1))
+        nacc = sum(o["n_local_accepted"] for o in lat.measure(reset=True))
+        proposals = (args.local_steps + 3) * sum(2 * ns * M for (_, M, ns) in shapes)
+        local_upd = {"value": world * args.local_steps / (ms_loc / 1e3), "unit": "sweeps/s",
+                     "steps": args.local_steps, "ms_per_sweep": ms_loc / args.local_steps,
+                     "accepted_per_proposal": nacc / proposals, "launches_per_sweep": 5}
     lat.close()
 
     # plain FP64 form: same kernels in double, one launch per phase, no graph
@@ -438,7 +457,7 @@ def main():
                 "particle_slice_updates_per_s": value * part_slices,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (nclasses + 2), "clocks": clocks, "fp64_plain": fp64,
-                "fp32_diagnostics": diag}
+                "fp32_diagnostics": diag, "local_update": local_upd}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

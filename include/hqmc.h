@@ -73,6 +73,7 @@ typedef struct {
      * n_nonpositive  filter amplitudes alpha_M(x_a) <= 0 (that log-weight is not finite). */
     int64_t n_degenerate;
     int64_t n_nonpositive;
+    int64_t n_local_accepted; /* local link moves accepted (hqmc_local_sweep) since the last reset */
 } hqmc_obs;
 
 /* Create a context for n_chains independent chains on CUDA device `device`.
@@ -176,6 +177,19 @@ int hqmc_attach_workspace(hqmc_ctx *ctx, void *dev_ptr, size_t bytes);
  * Numerical degeneracies are counted (hqmc_obs.n_degenerate, n_nonpositive), not raised.
  * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_TIMEOUT. */
 int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
+
+/* Run n_sweeps >= 0 local-update sweeps (Sec. 3.5.1, Eq. Rlocal, read in the position
+ * basis) on the context's stream, as an alternative or a complement to the FFBS sweep.
+ * One sweep proposes, for every worldline and slice l once, a move of x_l by one lattice
+ * step (+x, -x, +y, -y, uniform) with x_{l-1} and x_{l+1} held, accepted with probability
+ * min(1, R), R = G(x'-x_{l-1}) W_l(x') G(x_{l+1}-x') / [G(x-x_{l-1}) W_l(x) G(x_{l+1}-x)]
+ * in FP64 (M = 1: R = W_l(x')/W_l(x)).  Slices are visited by colour: even l, odd l, then
+ * l = M-1 alone when M is odd (slices of one colour are never neighbours).  Uniforms:
+ * Philox phase 4, i = sigma Nsig + p, j = 2l (step, floor(4u)) and 2l + 1 (accept iff
+ * u < R).  Then the same Gibbs step and observable accumulation as hqmc_sweep; the sweep
+ * counter advances.  Accepted moves are counted per chain (hqmc_obs.n_local_accepted).
+ * Plain launches (no graph).  Errors: HQMC_ERR_ARG, HQMC_ERR_STATE, HQMC_ERR_CUDA. */
+int hqmc_local_sweep(hqmc_ctx *ctx, int n_sweeps);
 
 /* Read the accumulated observables.  out: host array [n_chains] (nullable).
  * Sk, Cr (nullable, host) receive per chain the spin structure factor

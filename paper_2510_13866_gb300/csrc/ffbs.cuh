@@ -133,7 +133,9 @@ __device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_
     else cp_async8(sdst + sc, gsrc + gc);
 }
 
-template <typename T, int L>
+// BLK: the class has chains with FFBS blocks B < M (the closed-loop instantiation carries
+// none of the block bookkeeping)
+template <typename T, int L, bool BLK>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevState st, FfbsLaunch fl) {
     using G = FfbsGeo<T, L>;
     using V = vec2_t<T>;
@@ -182,10 +184,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         const int M = cd.M, Nsig = cd.Nsig;
         // unit = (pair, block): the blocks of a pair are independent given their held ends
         const int ru = int(q - fl.class_unit_off[lo]);
-        int sg, kp, len;
+        int sg, kp, len, a_keep = 0;
         {
-            const int Bk = ffbs_block_len(cd.block, M), nblk = ffbs_nblk(cd.block, M);
-            const int rr = ru / nblk, b = ru - rr * nblk;
+            const int Bk = BLK ? ffbs_block_len(cd.block, M) : M, nblk = BLK ? ffbs_nblk(cd.block, M) : 1;
+            const int rr = BLK ? ru / nblk : ru, b = BLK ? ru - rr * nblk : 0;
             sg = rr / cd.npair;
             kp = rr % cd.npair;
             // block b of the blocks of Bk slices from the anchor a, a+Bk, a+2Bk, ... (the
@@ -199,15 +201,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (l0 >= M) l0 -= M;
             len = (b + 1) * Bk <= M ? Bk : M - b * Bk;
             const int le = (l0 + len >= M) ? l0 + len - M : l0 + len;
-            __syncwarp(gmask);
-            if (gl == 0) {
-                meta[0] = b;
-                meta[1] = nblk;
-                meta[2] = rr;
-                meta[3] = l0;
-                meta[4] = le;
+            if constexpr (BLK) {
+                __syncwarp(gmask);
+                if (gl == 0) {
+                    meta[0] = b;
+                    meta[1] = nblk;
+                    meta[2] = rr;
+                    meta[3] = l0;
+                    meta[4] = le;
+                }
+            } else {
+                a_keep = a;  // the closed loop starts and ends at the anchor
+                (void)le;
             }
         }
+        auto first_slice = [&]() { if constexpr (BLK) return int(meta[3]); else return a_keep; };
+        auto end_slice = [&]() { if constexpr (BLK) return int(meta[4]); else return a_keep; };
         const int p0 = 2 * kp, p1 = 2 * kp + 1;
         const bool has1 = p1 < Nsig;
         const uint64_t wl0 = (uint64_t)sg * Nsig + p0, wl1 = (uint64_t)sg * Nsig + p1;
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
 
         // ---- forward filter ----
         __syncwarp(gmask);
-        const int l0 = meta[3];
+        const int l0 = first_slice();
         V v[L];
         {
             // the held end sites are re-read where they are used (short live ranges)
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             } else {
                 // alpha_{l0+len}(x_{l0+len}): final layout is C if len is odd
                 const bool finC = (len & 1) != 0;
-                const int le = meta[4];
+                const int le = end_slice();
                 const int xe0 = xp0[le];
                 const int xe1 = has1 ? int(xp1[le]) : xe0;
                 const int ex0 = xe0 % L, ey0 = xe0 / L, ex1 = xe1 % L, ey1 = xe1 / L;
@@ -348,8 +357,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             double *lw = st.logw + cd.logw_off;
-            const int b = meta[0], nblk = meta[1], rr = meta[2];
-            if (nblk == 1) {
+            const int b = BLK ? int(meta[0]) : 0, nblk = BLK ? int(meta[1]) : 1, rr = BLK ? int(meta[2]) : 0;
+            if (!BLK || nblk == 1) {
                 lw[wl0] = part0;
                 if (has1) lw[wl1] = part1;
             } else {
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         const float *hl = tb.h_f;
         int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
         float ek0 = 0.f, ek1 = 0.f;
-        const int le = meta[4];
+        const int le = end_slice();
         const int xs0 = xp0[l0];
         const int xs1 = has1 ? int(xp1[l0]) : xs0;
         const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;

@@ -13,7 +13,8 @@ namespace hqmc {
 template <typename T, int L>
 static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
-    ffbs_kernel<T, L><<<grid, wpc * 32, sm, s>>>(st, fl);
+    if (fl.blocks) ffbs_kernel<T, L, true><<<grid, wpc * 32, sm, s>>>(st, fl);
+    else ffbs_kernel<T, L, false><<<grid, wpc * 32, sm, s>>>(st, fl);
     return cudaGetLastError();
 }
 
@@ -21,9 +22,13 @@ static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, i
 template <typename T, int L>
 static cudaError_t ffbs_occ(int wpc, int *blocks) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
-    auto k = ffbs_kernel<T, L>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    auto kb = ffbs_kernel<T, L, true>;
+    cudaError_t e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
+    auto k = ffbs_kernel<T, L, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    // both instantiations are held to the same launch bounds; the closed-loop one sizes the grid
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, wpc * 32, sm);
 }
 

@@ -65,7 +65,7 @@ struct MeasAcc {
     unsigned long long degenerate;   // FFBS draws that met an all-zero CDF (the site was kept)
                                      // and forward slices with a non-finite normaliser
     unsigned long long nonpositive;  // filter amplitudes alpha_M(x_a) <= 0 (log-weight invalid)
-    double pad[1];
+    unsigned long long local_accepted;  // accepted local link moves
 };
 
 struct DevState {
@@ -108,6 +108,7 @@ struct FfbsLaunch {
     void *scratch;             // slots of len_max * L * L complex values
     long long slot_elems;      // complex elements per slot
     unsigned *next_unit;       // work counter: groups take units in order (zeroed per launch)
+    int blocks;                // some chain of the class has FFBS blocks B < M
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.
@@ -144,6 +145,10 @@ cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, 
 cudaError_t configure_slice();
 void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
+// local link updates: the largest (worldline, slice) count of one colour of a chain, and
+// one launch over every chain for one colour (0, 1, 2)
+int local_max_units(int M, int Nsig);
+cudaError_t launch_local(const DevState &st, int nchains, int max_units, int color, cudaStream_t stream);
 cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStream_t stream);
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
                            double *sk_out, long long total_N, cudaStream_t stream);

@@ -603,6 +603,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.class_unit_off = cls + n + (n + 1) + 1;
         fl.total_units = cl.total_units;
         fl.len_max = cl.len_max;
+        fl.blocks = cl.total_units != cl.total_pairs ? 1 : 0;
         fl.scratch = c->base + cl.scratch_off;
         fl.slot_elems = (long long)cl.len_max * cl.L * cl.L;
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
@@ -982,6 +983,32 @@ int hqmc_sweep(hqmc_ctx *c, int n_sweeps, double *logw_out) {
     return check_status(c);
 }
 
+int hqmc_local_sweep(hqmc_ctx *c, int n_sweeps) {
+    if (!c || n_sweeps < 0) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    int max_units = 0, max_M = 0, max_L = 0;
+    for (auto &d : c->cdev) {
+        max_units = std::max(max_units, local_max_units(d.M, d.Nsig));
+        max_M = std::max(max_M, d.M);
+        max_L = std::max(max_L, d.L);
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        for (int color = 0; color < 3; ++color) {
+            cudaError_t e = launch_local(c->st, c->nchains, max_units, color, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "local launch");
+        }
+        cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, c->slices_per_cta, true, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
+        e = launch_advance(c->st, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
+    }
+    c->sweeps_host += n_sweeps;
+    if (n_sweeps > 0) c->started = true;
+    return check_status(c);
+}
+
 int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) {
     if (!c) return HQMC_ERR_ARG;
     if (!c->ready) return fail(c, HQMC_ERR_STATE, "no state yet");
@@ -1011,6 +1038,7 @@ int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) 
             o.s_pipi = skh[d.meas_off + kh + d.L * kh];
             o.n_degenerate = (int64_t)acc[i].degenerate;
             o.n_nonpositive = (int64_t)acc[i].nonpositive;
+            o.n_local_accepted = (int64_t)acc[i].local_accepted;
         }
     }
     if (reset) {

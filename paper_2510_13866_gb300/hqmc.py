@@ -34,6 +34,7 @@ SIGNATURES = {
     "hqmc_workspace_size": (_i, [_vp, C.POINTER(_sz)]),
     "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
+    "hqmc_local_sweep": (_i, [_vp, _i]),
     "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
     "hqmc_set_checkpoint": (_i, [_vp, _i, _i]),
     "hqmc_log_weight_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -61,7 +62,7 @@ class HQMCError(RuntimeError):
 class Obs(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("density", C.c_double), ("double_occ", C.c_double),
                 ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double),
-                ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64)]
+                ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64), ("n_local_accepted", C.c_int64)]
 
 
 _lib = None
@@ -254,6 +255,12 @@ class Lattice:
             o += 2 * ns
         return out
 
+    def local_sweep(self, n=1):
+        """Run n local-update sweeps (single-slice Metropolis moves of every worldline,
+        then the Gibbs step and observables)."""
+        self.prepare()
+        self._check(lib().hqmc_local_sweep(self._ctx, int(n)))
+
     def measure(self, reset=False):
         self.prepare()
         obs = (Obs * self.n_chains)()
@@ -267,7 +274,8 @@ class Lattice:
             ob = obs[c]
             res.append(dict(n_samples=ob.n_samples, density=ob.density, double_occ=ob.double_occ, m2=ob.m2,
                             ekin=ob.ekin, s_pipi=ob.s_pipi, n_degenerate=ob.n_degenerate,
-                            n_nonpositive=ob.n_nonpositive, Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
+                            n_nonpositive=ob.n_nonpositive, n_local_accepted=ob.n_local_accepted,
+                            Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
             o += N
         return res
 
