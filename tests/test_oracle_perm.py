@@ -106,12 +106,13 @@ def free_two_worldlines(L, t, beta):
 
 @pytest.mark.parametrize("with_local", [False, True])
 def test_free_worldlines_sample_the_fermionic_closed_forms(with_local):
-    """U = 0, L = 3, two worldlines per spin, t = 1, beta = 2, dtau = 0.5 (M = 4).
+    """U = 0, L = 3, two worldlines per spin, t = 1, beta = 0.5, dtau = 0.25 (M = 2), where
+    P(swap) = 0.22 and E[sgn] = 0.57 per spin.
     Independent chains (30 sweeps each, optionally each followed by a local sweep) give
     P(swap) and E[sgn] per spin within 4 standard errors of Tr(T^2)/(Tr(T)^2 + Tr(T^2))
     and its companion; without local sweeps, the sign-reweighted link estimator of one
     spin, E[sgn sum links] / E[sgn], lies within 4 standard errors of d log Z_F / dt."""
-    L, t, beta, dtau = 3, 1.0, 2.0, 0.5
+    L, t, beta, dtau = 3, 1.0, 0.5, 0.25
     p_swap, e_sgn, dlogzf = free_two_worldlines(L, t, beta)
     swapped, sg_links, sgns = [], [], []
     for seed in range(800):
@@ -137,6 +138,7 @@ def test_free_worldlines_sample_the_fermionic_closed_forms(with_local):
         est = num.mean() / den.mean()
         z = num - est * den
         se_r = z.std(ddof=1) / np.sqrt(n) / abs(den.mean())
+        assert se_r < 0.05 * abs(dlogzf)
         assert abs(est - dlogzf) < 4 * se_r, (est, dlogzf, se_r)
 
 
