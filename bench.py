@@ -269,6 +269,8 @@ def main():
                          "(M=1024); grad16 times the adjoint")
     ap.add_argument("--local-steps", type=int, default=20,
                     help="local-update sweeps timed beside the FFBS sweep (0: skip)")
+    ap.add_argument("--perm", action="store_true",
+                    help="permutation updates at tau = beta in every sweep (sign-reweighted observables)")
     ap.add_argument("--block", type=int, default=0,
                     help="FFBS block length B (0: the closed loop from the anchor, the default)")
     ap.add_argument("--beta", type=float, default=None,
@@ -319,6 +321,8 @@ def main():
                 lt.set_params(*p, chain=c)
         if args.block:
             lt.set_block(args.block)
+        if args.perm:
+            lt.set_permutations(True)
         lt.prepare()
         return lt
 
@@ -446,6 +450,8 @@ def main():
             wl = wl.replace("1 chain", f"{nchains} chains")
         if args.block:
             wl += f"; block FFBS, B={args.block}"
+        if args.perm:
+            wl += "; permutation updates at tau = beta"
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -74,6 +74,11 @@ typedef struct {
     int64_t n_degenerate;
     int64_t n_nonpositive;
     int64_t n_local_accepted; /* local link moves accepted (hqmc_local_sweep) since the last reset */
+    /* With permutations (hqmc_set_permutations) the sampled weight is |w| and every average
+     * above is sign-reweighted, <O> = sum(O s) / sum(s) over the measured sweeps with
+     * s = sgn(P_up) sgn(P_dn) (Eq. reweight); without them s = +1. */
+    double mean_sign;         /* sum(s) / n_samples */
+    int64_t n_perm_accepted;  /* permutation swaps accepted since the last reset */
 } hqmc_obs;
 
 /* Create a context for n_chains independent chains on CUDA device `device`.
@@ -190,6 +195,27 @@ int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
  * counter advances.  Accepted moves are counted per chain (hqmc_obs.n_local_accepted).
  * Plain launches (no graph).  Errors: HQMC_ERR_ARG, HQMC_ERR_STATE, HQMC_ERR_CUDA. */
 int hqmc_local_sweep(hqmc_ctx *ctx, int n_sweeps);
+
+/* Permutation updates at tau = beta (Sec. 3.5.3).  on = 1: every later hqmc_sweep first
+ * proposes, for each chain and spin, pair swaps of successors P'(p) = P(q), P'(q) = P(p)
+ * over the disjoint pairs (2k + r, 2k + 1 + r) mod Nsig, k < Nsig/2, with the rotation
+ * r = floor(u Nsig) (Philox phase 5, i = sigma, j = 0), each accepted iff u < R (phase 5,
+ * j = 1 + k), R = G(x_0^{P(q)} - x_{M-1}^p) G(x_0^{P(p)} - x_{M-1}^q) /
+ * [G(x_0^{P(p)} - x_{M-1}^p) G(x_0^{P(q)} - x_{M-1}^q)] in FP64; each accepted swap flips
+ * the chain's sign.  The FFBS of the sweep then runs every worldline's unit from slice a of
+ * p to slice a of P(p) (slices a+1..M-1 of p, then 0..a-1 of P(p), both slice-a sites
+ * held), local sweeps link slice M-1 of p to slice 0 of P(p), and the observables are
+ * sign-reweighted (hqmc_obs).  The permutation starts at the identity and is kept when
+ * the updates are turned off again.  The adjoint then returns HQMC_ERR_UNSUPPORTED.
+ * Errors: HQMC_ERR_STATE (set_params missing), HQMC_ERR_UNSUPPORTED (a chain with M < 2). */
+int hqmc_set_permutations(hqmc_ctx *ctx, int on);
+
+/* The permutations of chain c, perm [2][Nsig] (host, int32: perm[sigma][p] = P(p)), and
+ * sign = sgn(P_up) sgn(P_dn); either may be NULL.  hqmc_set_perm overwrites them (each row
+ * must be a permutation of 0..Nsig-1; the sign follows from the parities).
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_STATE, HQMC_ERR_CUDA. */
+int hqmc_get_perm(hqmc_ctx *ctx, int chain, int32_t *perm, int *sign);
+int hqmc_set_perm(hqmc_ctx *ctx, int chain, const int32_t *perm);
 
 /* Read the accumulated observables.  out: host array [n_chains] (nullable).
  * Sk, Cr (nullable, host) receive per chain the spin structure factor

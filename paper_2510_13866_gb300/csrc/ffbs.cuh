@@ -133,8 +133,10 @@ __device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_
     else cp_async8(sdst + sc, gsrc + gc);
 }
 
-// BLK: the class has chains with FFBS blocks B < M (the closed-loop instantiation carries
-// none of the block bookkeeping)
+// BLK: the general work units -- FFBS blocks B < M and/or a permutation at tau = beta (the
+// closed-loop instantiation carries none of that bookkeeping).  With a permutation P the
+// unit of worldline p runs from slice a of p to slice a of P(p): its positions at or past
+// the wrap (a + offset >= M) are slices of worldline P(p).
 template <typename T, int L, bool BLK>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevState st, FfbsLaunch fl) {
     using G = FfbsGeo<T, L>;
@@ -155,8 +157,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     T *g2 = reinterpret_cast<T *>(gsm + G::XBUF + G::MIXB);
     V *wx = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B);
     V *rb = reinterpret_cast<V *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB);  // [2][L]
-    // block bookkeeping of the current unit (b, nblk, pair, l0, l0+len), parked in shared
-    // memory across the forward loop instead of in registers
+    // bookkeeping of the current unit (b, nblk, pair, l0, l0+len, first position past the
+    // wrap, successors of both worldlines), parked in shared memory across the forward loop
+    // instead of in registers
     volatile int *meta = reinterpret_cast<volatile int *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB + G::RBB);
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
     const long long ngroups = (long long)gridDim.x * wpc * G::GPW;
@@ -204,11 +207,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if constexpr (BLK) {
                 __syncwarp(gmask);
                 if (gl == 0) {
+                    const int *P = st.perm + cd.perm_off + sg * Nsig;
                     meta[0] = b;
                     meta[1] = nblk;
                     meta[2] = rr;
                     meta[3] = l0;
                     meta[4] = le;
+                    meta[5] = M - a - b * Bk;  // block positions >= this lie past the wrap
+                    meta[6] = P[2 * kp];
+                    meta[7] = (2 * kp + 1 < Nsig) ? P[2 * kp + 1] : P[2 * kp];
                 }
             } else {
                 a_keep = a;  // the closed loop starts and ends at the anchor
@@ -217,14 +224,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         }
         auto first_slice = [&]() { if constexpr (BLK) return int(meta[3]); else return a_keep; };
         auto end_slice = [&]() { if constexpr (BLK) return int(meta[4]); else return a_keep; };
+        // the sites of both worldlines at block position i (slice l): past the wrap they
+        // are the successors' (general units only)
+        int16_t *xspin = st.x + cd.x_off + (long long)sg * Nsig * M;
+        auto owner0 = [&](int i) -> int16_t * {
+            if constexpr (BLK) return xspin + (long long)(i >= meta[5] ? meta[6] : 2 * kp) * M;
+            else return xspin + (long long)(2 * kp) * M;
+        };
+        auto owner1 = [&](int i) -> int16_t * {
+            if constexpr (BLK) return xspin + (long long)(i >= meta[5] ? meta[7] : 2 * kp + 1) * M;
+            else return xspin + (long long)(2 * kp + 1) * M;
+        };
         const int p0 = 2 * kp, p1 = 2 * kp + 1;
         const bool has1 = p1 < Nsig;
         const uint64_t wl0 = (uint64_t)sg * Nsig + p0, wl1 = (uint64_t)sg * Nsig + p1;
         const T wp = T(cd.w_plus[sg]), wm = T(cd.w_minus[sg]);
         const uint32_t *srow = st.sbits + cd.s_off;
         const uint32_t *scol = srow + (long long)M * L * cd.wpl;
-        int16_t *xp0 = st.x + cd.x_off + (long long)wl0 * M;
-        int16_t *xp1 = st.x + cd.x_off + (long long)wl1 * M;
 
         // line-convolution constants and the doubled real-space kernel g2[j] = g(j mod L)
         __syncwarp(gmask);
@@ -242,8 +258,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         V v[L];
         {
             // the held end sites are re-read where they are used (short live ranges)
-            const int xs0 = xp0[l0];
-            const int xs1 = has1 ? int(xp1[l0]) : xs0;  // a missing partner shadows worldline 0
+            const int xs0 = owner0(0)[l0];
+            const int xs1 = has1 ? int(owner1(0)[l0]) : xs0;  // a missing partner shadows worldline 0
             const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
             // f_{l0} = W_{l0}(x_{l0}) delta_{x_{l0}}, layout R: lane = iy, register = ix
             T wv0, wv1;
@@ -336,8 +352,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 // alpha_{l0+len}(x_{l0+len}): final layout is C if len is odd
                 const bool finC = (len & 1) != 0;
                 const int le = end_slice();
-                const int xe0 = xp0[le];
-                const int xe1 = has1 ? int(xp1[le]) : xe0;
+                const int xe0 = owner0(len)[le];
+                const int xe1 = has1 ? int(owner1(len)[le]) : xe0;
                 const int ex0 = xe0 % L, ey0 = xe0 / L, ex1 = xe1 % L, ey1 = xe1 / L;
                 const int own0 = finC ? ex0 : ey0, reg0 = finC ? ey0 : ex0;
                 const int own1 = finC ? ex1 : ey1, reg1 = finC ? ey1 : ex1;
@@ -399,11 +415,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
         float ek0 = 0.f, ek1 = 0.f;
         const int le = end_slice();
-        const int xs0 = xp0[l0];
-        const int xs1 = has1 ? int(xp1[l0]) : xs0;
+        const int xs0 = owner0(0)[l0];
+        const int xs1 = has1 ? int(owner1(0)[l0]) : xs0;
         const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
-        int cur0 = xp0[le];
-        int cur1 = has1 ? int(xp1[le]) : cur0;
+        int cur0 = owner0(len)[le];
+        int cur1 = has1 ? int(owner1(len)[le]) : cur0;
         if (gl == 0) {
             atomicAdd(hist_s + (long long)l0 * N + xs0, 1);
             if (has1) atomicAdd(hist_s + (long long)l0 * N + xs1, 1);
@@ -561,11 +577,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (gl == 0) {
                 // link x_l -> x_{l+1}
                 ek0 += hl[(cx0 - nxt0 % L + L) % L] + hl[(cy0 - nxt0 / L + L) % L];
-                xp0[lb] = int16_t(nxt0);
+                owner0(i)[lb] = int16_t(nxt0);
                 atomicAdd(hist_s + (long long)lb * N + nxt0, 1);
                 if (has1) {
                     ek1 += hl[(cx1 - nxt1 % L + L) % L] + hl[(cy1 - nxt1 / L + L) % L];
-                    xp1[lb] = int16_t(nxt1);
+                    owner1(i)[lb] = int16_t(nxt1);
                     atomicAdd(hist_s + (long long)lb * N + nxt1, 1);
                 }
             }
@@ -576,7 +592,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             // link x_{l0} -> x_{l0+1}
             ek0 += hl[(cur0 % L - sx0 + L) % L] + hl[(cur0 / L - sy0 + L) % L];
             if (has1) ek1 += hl[(cur1 % L - sx1 + L) % L] + hl[(cur1 / L - sy1 + L) % L];
-            atomicAdd(&st.meas[c].link_sum, double(ek0) + (has1 ? double(ek1) : 0.0));
+            double eks = double(ek0) + (has1 ? double(ek1) : 0.0);
+            if constexpr (BLK) eks *= chain_sign(st, c);  // sign-weighted with permutations
+            atomicAdd(&st.meas[c].link_sum, eks);
         }
         __syncwarp(gmask);
     }

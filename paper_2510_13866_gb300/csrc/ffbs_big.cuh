@@ -223,8 +223,12 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         const int wpl = cd.wpl;
         const uint32_t *srow = st.sbits + cd.s_off;
         const uint32_t *scol = srow + (long long)M * L * wpl;
-        int16_t *xp0 = st.x + cd.x_off + (long long)wl0 * M;
-        int16_t *xp1 = st.x + cd.x_off + (long long)wl1 * M;
+        // with a permutation P the unit of p runs from slice a of p to slice a of P(p): its
+        // block positions at or past the wrap are slices of the successors q0 = P(p0),
+        // q1 = P(p1) (the identity: the closed loops)
+        int16_t *xspin = st.x + cd.x_off + (long long)sg * Nsig * M;
+        const int *Pp = st.perm + cd.perm_off + sg * Nsig;
+        const int q0 = Pp[p0], q1 = has1 ? Pp[p1] : q0;
 
         __syncthreads();
         for (int j = tid; j < L; j += NT) mix[j] = vsplat(tb.mix_f[j]);
@@ -249,13 +253,16 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         if (l0 >= M) l0 -= M;
         const int len = (b + 1) * Bk <= M ? Bk : M - b * Bk;
         const int le = (l0 + len >= M) ? l0 + len - M : l0 + len;
+        const int wi = M - a - b * Bk;  // block positions >= wi lie past the wrap
+        auto owner0 = [&](int i) { return xspin + (long long)(i >= wi ? q0 : p0) * M; };
+        auto owner1 = [&](int i) { return xspin + (long long)(i >= wi ? q1 : p1) * M; };
 
         // ---- forward filter ----
         __syncthreads();
         V v[E];
         {
-            const int xs0 = xp0[l0];
-            const int xs1 = has1 ? int(xp1[l0]) : xs0;
+            const int xs0 = owner0(0)[l0];
+            const int xs1 = has1 ? int(owner1(0)[l0]) : xs0;
             const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
             T wv0, wv1;
             if (cd.gauss) {
@@ -337,8 +344,8 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             } else {
                 // alpha_{l0+len}(x_{l0+len}): final layout is C (lines = x) if len is odd
                 const bool finC = (len & 1) != 0;
-                const int xe0 = xp0[le];
-                const int xe1 = has1 ? int(xp1[le]) : xe0;
+                const int xe0 = owner0(len)[le];
+                const int xe1 = has1 ? int(owner1(len)[le]) : xe0;
                 const int ex0 = xe0 % L, ey0 = xe0 / L, ex1 = xe1 % L, ey1 = xe1 / L;
                 const int own0 = finC ? ex0 : ey0, pos0 = finC ? ey0 : ex0;
                 const int own1 = finC ? ex1 : ey1, pos1 = finC ? ey1 : ex1;
@@ -401,11 +408,11 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
         };
         __syncthreads();
         if (len > 1) prefetch(len - 1);
-        const int xs0 = xp0[l0];
-        const int xs1 = has1 ? int(xp1[l0]) : xs0;
+        const int xs0 = owner0(0)[l0];
+        const int xs1 = has1 ? int(owner1(0)[l0]) : xs0;
         const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
-        int cur0 = xp0[le];
-        int cur1 = has1 ? int(xp1[le]) : cur0;
+        int cur0 = owner0(len)[le];
+        int cur1 = has1 ? int(owner1(len)[le]) : cur0;
         if (tid == 0) {
             atomicAdd(hist_s + (long long)l0 * N + xs0, 1);
             if (has1) atomicAdd(hist_s + (long long)l0 * N + xs1, 1);
@@ -541,11 +548,11 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             }
             if (tid == 0) {
                 ek0 += hl[(cx0 - nxt0 % L + L) % L] + hl[(cy0 - nxt0 / L + L) % L];
-                xp0[lb] = int16_t(nxt0);
+                owner0(i)[lb] = int16_t(nxt0);
                 atomicAdd(hist_s + (long long)lb * N + nxt0, 1);
                 if (has1) {
                     ek1 += hl[(cx1 - nxt1 % L + L) % L] + hl[(cy1 - nxt1 / L + L) % L];
-                    xp1[lb] = int16_t(nxt1);
+                    owner1(i)[lb] = int16_t(nxt1);
                     atomicAdd(hist_s + (long long)lb * N + nxt1, 1);
                 }
             }
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
             // link x_{l0} -> x_{l0+1}
             ek0 += hl[(cur0 % L - sx0 + L) % L] + hl[(cur0 / L - sy0 + L) % L];
             if (has1) ek1 += hl[(cur1 % L - sx1 + L) % L] + hl[(cur1 / L - sy1 + L) % L];
-            atomicAdd(&st.meas[c].link_sum, double(ek0) + (has1 ? double(ek1) : 0.0));
+            atomicAdd(&st.meas[c].link_sum, (double(ek0) + (has1 ? double(ek1) : 0.0)) * chain_sign(st, c));
         }
     }
 }

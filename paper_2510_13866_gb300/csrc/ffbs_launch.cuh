@@ -13,7 +13,7 @@ namespace hqmc {
 template <typename T, int L>
 static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
-    if (fl.blocks) ffbs_kernel<T, L, true><<<grid, wpc * 32, sm, s>>>(st, fl);
+    if (fl.general) ffbs_kernel<T, L, true><<<grid, wpc * 32, sm, s>>>(st, fl);
     else ffbs_kernel<T, L, false><<<grid, wpc * 32, sm, s>>>(st, fl);
     return cudaGetLastError();
 }

@@ -53,6 +53,7 @@ struct ChainDev {
     long long logw_off; // double offset of log-weights [2][Nsig]
     long long v_off;    // element offset of [2][M][N] gradient arrays
     long long meas_off; // offset into the measurement arrays (N per chain)
+    long long perm_off; // int offset of the permutation P [2][Nsig] then its inverse [2][Nsig]
 };
 
 // Per-chain measurement accumulators (device, zeroed at reset).
@@ -66,7 +67,11 @@ struct MeasAcc {
                                      // and forward slices with a non-finite normaliser
     unsigned long long nonpositive;  // filter amplitudes alpha_M(x_a) <= 0 (log-weight invalid)
     unsigned long long local_accepted;  // accepted local link moves
+    long long sign_sum;                 // sum over measured sweeps of sgn(P_up) sgn(P_dn)
+    unsigned long long perm_accepted;   // accepted permutation swaps
 };
+// The sums n_sum, d_sum, m2_sum, link_sum and S(k) are weighted by the sweep's sign
+// (two's complement in the unsigned counters); with permutations off the sign is +1.
 
 struct DevState {
     const ChainDev *chains;
@@ -86,6 +91,8 @@ struct DevState {
     int gw_f64;          // W stored as double (FP64 context) or float
     double *logw_part;   // per-block log-weight partials of block FFBS
     unsigned *blk_done;  // per-pair counters of finished blocks (zero between sweeps)
+    int *perm;           // permutations at tau = beta and their inverses (perm_off per chain)
+    unsigned *parity;    // per chain: bit 0 = parity of P_up P_dn (sign -1 when set)
 };
 
 // Blocks of the FFBS loop of a chain: length B (0 or >= M: one block of M slices) and count.
@@ -108,7 +115,8 @@ struct FfbsLaunch {
     void *scratch;             // slots of len_max * L * L complex values
     long long slot_elems;      // complex elements per slot
     unsigned *next_unit;       // work counter: groups take units in order (zeroed per launch)
-    int blocks;                // some chain of the class has FFBS blocks B < M
+    int general;               // some chain has FFBS blocks B < M, or the context has used
+                               // permutations: the general work-unit instantiation runs
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.
@@ -149,6 +157,10 @@ cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
 // one launch over every chain for one colour (0, 1, 2)
 int local_max_units(int M, int Nsig);
 cudaError_t launch_local(const DevState &st, int nchains, int max_units, int color, cudaStream_t stream);
+// one permutation update (pair swaps at tau = beta) of every chain and spin
+cudaError_t launch_perm(const DevState &st, int nchains, int max_pairs, cudaStream_t stream);
+
+__device__ __forceinline__ int chain_sign(const DevState &st, int c) { return (st.parity[c] & 1u) ? -1 : 1; }
 cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStream_t stream);
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
                            double *sk_out, long long total_N, cudaStream_t stream);

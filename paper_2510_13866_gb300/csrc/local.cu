@@ -6,7 +6,16 @@
 // a handful of table lookups per move.  Slices of one colour (even l; odd l; l = M-1 alone
 // when M is odd) are never neighbours in imaginary time, so one launch per colour updates
 // all of them at once: one thread per (chain, worldline, slice of the colour).  The
-// occupancy histogram and the kinetic link sums of the final paths are fused in.
+// occupancy histogram and the kinetic link sums of the final paths are fused in.  With a
+// permutation P at tau = beta, slice 0 of p follows slice M-1 of P^{-1}(p) and slice M-1
+// of p precedes slice 0 of P(p) (other colours when M >= 2).
+//
+// The permutation update (Sec. 3.5.3) is here too: pair swaps of successors,
+// P'(p) = P(q), P'(q) = P(p), accepted with probability min(1, R),
+//     R = G(x_0^{P(q)} - x_{M-1}^p) G(x_0^{P(p)} - x_{M-1}^q)
+//         / [G(x_0^{P(p)} - x_{M-1}^p) G(x_0^{P(q)} - x_{M-1}^q)],
+// over disjoint pairs (2k + r, 2k + 1 + r) mod Nsig with a random rotation r, one thread
+// per pair; every accepted swap flips the chain's sign.
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -59,10 +68,14 @@ __global__ void __launch_bounds__(kLocalThreads) local_kernel(DevState st, int c
         const ChainTab &tb = st.tabs[c];
         const int wl = int(u / cnt), k = int(u % cnt);
         const int l = color == 2 ? M - 1 : 2 * k + color;
-        const int sg = wl / Nsig;
+        const int sg = wl / Nsig, p = wl - sg * Nsig;
+        const int16_t *xspin = st.x + cd.x_off + (long long)sg * Nsig * M;
         int16_t *xp = st.x + cd.x_off + (long long)wl * M;
         const int lm = l == 0 ? M - 1 : l - 1, ln = l + 1 == M ? 0 : l + 1;
-        const int xm = xp[lm], x = xp[l], xn = xp[ln];
+        const int *P = st.perm + cd.perm_off + sg * Nsig, *Pinv = P + 2 * Nsig;
+        const int xm = l == 0 ? xspin[(long long)Pinv[p] * M + lm] : xp[lm];
+        const int xn = l + 1 == M ? xspin[(long long)P[p] * M] : xp[ln];
+        const int x = xp[l];
         // uniforms: phase 4, i = worldline, j = 2l (step) and 2l + 1 (acceptance)
         const u64x4 w4 = philox4x64_10((uint64_t)(l >> 1), (uint64_t)wl, 4, *st.sweep, cd.seed, 0);
         const double u0 = u53((l & 1) ? w4.v[2] : w4.v[0]), u1 = u53((l & 1) ? w4.v[3] : w4.v[1]);
@@ -77,7 +90,8 @@ __global__ void __launch_bounds__(kLocalThreads) local_kernel(DevState st, int c
         const double *g = tb.g_d;
         double R;
         if (M == 1) {
-            R = slice_w(st, cd, sg, l, xnew) / slice_w(st, cd, sg, l, x);  // the link G(0) stays
+            // closed on itself (permutations need M >= 2): the link G(0) stays
+            R = slice_w(st, cd, sg, l, xnew) / slice_w(st, cd, sg, l, x);
         } else {
             const double num = G2(g, L, xm, xnew) * slice_w(st, cd, sg, l, xnew) * G2(g, L, xnew, xn);
             const double den = G2(g, L, xm, x) * slice_w(st, cd, sg, l, x) * G2(g, L, x, xn);
@@ -100,12 +114,59 @@ __global__ void __launch_bounds__(kLocalThreads) local_kernel(DevState st, int c
     for (int o = 16; o > 0; o >>= 1) ek += __shfl_xor_sync(0xffffffffu, ek, o);
     const unsigned nacc = __popc(__ballot_sync(0xffffffffu, accepted));
     if ((threadIdx.x & 31) == 0) {
-        if (ek != 0.f) atomicAdd(&st.meas[c].link_sum, double(ek));
+        if (ek != 0.f) atomicAdd(&st.meas[c].link_sum, double(ek) * chain_sign(st, c));
         if (nacc) atomicAdd(&st.meas[c].local_accepted, (unsigned long long)nacc);
     }
 }
 
+__global__ void __launch_bounds__(kLocalThreads) perm_kernel(DevState st) {
+    const int c = blockIdx.y, sg = blockIdx.z;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, M = cd.M, Nsig = cd.Nsig, npr = Nsig / 2;
+    const uint64_t sweep = *st.sweep;
+    // pairing rotation (phase 5, i = sigma, j = 0)
+    int r = int(u53(philox4x64_10(0, (uint64_t)sg, 5, sweep, cd.seed, 0).v[0]) * Nsig);
+    if (r >= Nsig) r = Nsig - 1;
+    int *P = st.perm + cd.perm_off + sg * Nsig, *Pinv = P + 2 * Nsig;
+    const int16_t *X = st.x + cd.x_off + (long long)sg * Nsig * M;
+    const double *g = st.tabs[c].g_d;
+    unsigned cnt = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npr; k += gridDim.x * blockDim.x) {
+        int p = 2 * k + r, q = 2 * k + 1 + r;
+        if (p >= Nsig) p -= Nsig;
+        if (q >= Nsig) q -= Nsig;
+        const int Pp = P[p], Pq = P[q];
+        const int xlp = X[(long long)p * M + M - 1], xlq = X[(long long)q * M + M - 1];
+        const int a0 = X[(long long)Pp * M], b0 = X[(long long)Pq * M];
+        const double R = (G2(g, L, xlp, b0) * G2(g, L, xlq, a0)) / (G2(g, L, xlp, a0) * G2(g, L, xlq, b0));
+        // pair k: phase 5, i = sigma, j = 1 + k
+        const u64x4 w4 = philox4x64_10((uint64_t)((1 + k) >> 2), (uint64_t)sg, 5, sweep, cd.seed, 0);
+        const int wsel = (1 + k) & 3;
+        const double u = u53(wsel == 0 ? w4.v[0] : wsel == 1 ? w4.v[1] : wsel == 2 ? w4.v[2] : w4.v[3]);
+        if (u < R) {
+            P[p] = Pq;
+            P[q] = Pp;
+            Pinv[Pq] = p;
+            Pinv[Pp] = q;
+            ++cnt;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) {
+        atomicAdd(&st.meas[c].perm_accepted, (unsigned long long)cnt);
+        if (cnt & 1u) atomicXor(&st.parity[c], 1u);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_perm(const DevState &st, int nchains, int max_pairs, cudaStream_t stream) {
+    if (max_pairs <= 0) return cudaSuccess;
+    const dim3 grid(std::min((max_pairs + kLocalThreads - 1) / kLocalThreads, 64), nchains, 2);
+    perm_kernel<<<grid, kLocalThreads, 0, stream>>>(st);
+    return cudaGetLastError();
+}
 
 int local_max_units(int M, int Nsig) {
     int m = 0;

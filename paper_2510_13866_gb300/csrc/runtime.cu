@@ -84,6 +84,8 @@ struct hqmc_ctx {
     bool use_graph = true, persistent = true;
     int wpc = 0;
     int slices_per_cta = 4;  // Gibbs/measure kernel: slices handled by one CTA
+    bool perm_on = false;    // permutation updates at tau = beta in every sweep
+    bool perm_used = false;  // a permutation other than the identity may be in the state
     int num_sms = 0;
     std::string err;
 
@@ -113,6 +115,8 @@ struct hqmc_ctx {
     std::vector<uint32_t> keep_bits;
     std::vector<int16_t> keep_x;
     std::vector<double> keep_sig;
+    std::vector<int> keep_perm;
+    std::vector<unsigned> keep_parity;
     unsigned long long keep_sweep = 0;
     bool keep_started = false;
 
@@ -324,7 +328,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     };
     const size_t o_chains = take(sizeof(ChainDev) * nc);
     const size_t o_tabs = take(sizeof(ChainTab) * nc);
-    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0, gb = 0, pb = 0, db = 0;
+    long long sb = 0, xb = 0, hb = 0, lb = 0, vb = 0, mb = 0, gb = 0, pb = 0, db = 0, qb = 0;
     for (int i = 0; i < nc; ++i) {
         const HostChain &h = c->ch[i];
         ChainDev &d = c->cdev[i];
@@ -347,6 +351,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         const int nblk = ffbs_nblk(h.block, h.M);
         d.lwp_off = pb;
         d.done_off = db;
+        d.perm_off = qb;
+        qb += 4LL * h.Nsig;  // P [2][Nsig], then P^{-1} [2][Nsig]
         if (nblk > 1) {
             pb += 2LL * h.Nsig * nblk;
             db += 2LL * d.npair;
@@ -384,6 +390,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     const size_t o_gw = take(size_t(gb) * 2 * (f64 ? 8 : 4));
     const size_t o_lp = take(size_t(pb) * 8);
     const size_t o_bd = take(size_t(db) * 4);
+    const size_t o_pm = take(size_t(qb) * 4);
+    const size_t o_par = take(size_t(nc) * 4);
     c->off_cr = take(size_t(mb) * 8);
     c->off_sko = take(size_t(mb) * 8);
     // classes
@@ -445,6 +453,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     c->st.gw_f64 = f64 ? 1 : 0;
     c->st.logw_part = reinterpret_cast<double *>(o_lp);
     c->st.blk_done = reinterpret_cast<unsigned *>(o_bd);
+    c->st.perm = reinterpret_cast<int *>(o_pm);
+    c->st.parity = reinterpret_cast<unsigned *>(o_par);
     return HQMC_OK;
 }
 
@@ -492,6 +502,8 @@ int prepare(hqmc_ctx *c) {
     s.gw = rebase(s.gw, c->base);
     s.logw_part = rebase(s.logw_part, c->base);
     s.blk_done = rebase(s.blk_done, c->base);
+    s.perm = rebase(s.perm, c->base);
+    s.parity = rebase(s.parity, c->base);
     c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
     c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
     cudaStream_t st = c->stream;
@@ -514,6 +526,16 @@ int prepare(hqmc_ctx *c) {
         if (rc) return rc;
     }
     HQMC_CUDA(c, configure_slice());
+    {
+        // permutations start at the identity (and so do their inverses); parity 0 = sign +1
+        std::vector<int> ident;
+        for (auto &d : c->cdev)
+            for (int r = 0; r < 4; ++r)
+                for (int p = 0; p < d.Nsig; ++p) ident.push_back(p);
+        if (!ident.empty())
+            HQMC_CUDA(c, cudaMemcpyAsync(s.perm, ident.data(), ident.size() * 4, cudaMemcpyHostToDevice, st));
+        HQMC_CUDA(c, cudaStreamSynchronize(st));
+    }
     cudaError_t e = launch_init_state(s, c->nchains, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "init_state");
     HQMC_CUDA(c, cudaStreamSynchronize(st));
@@ -524,6 +546,10 @@ int prepare(hqmc_ctx *c) {
         HQMC_CUDA(c, cudaMemcpy(c->st.sbits, c->keep_bits.data(), c->keep_bits.size() * 4, cudaMemcpyHostToDevice));
         HQMC_CUDA(c, cudaMemcpy(c->st.x, c->keep_x.data(), c->keep_x.size() * 2, cudaMemcpyHostToDevice));
         HQMC_CUDA(c, cudaMemcpy(c->st.sweep, &c->keep_sweep, 8, cudaMemcpyHostToDevice));
+        if (!c->keep_perm.empty()) {
+            HQMC_CUDA(c, cudaMemcpy(c->st.perm, c->keep_perm.data(), c->keep_perm.size() * 4, cudaMemcpyHostToDevice));
+            HQMC_CUDA(c, cudaMemcpy(c->st.parity, c->keep_parity.data(), c->keep_parity.size() * 4, cudaMemcpyHostToDevice));
+        }
         if (!c->keep_sig.empty()) {
             HQMC_CUDA(c, cudaMemcpy(c->st.gsig, c->keep_sig.data(), c->keep_sig.size() * 8, cudaMemcpyHostToDevice));
             for (int i = 0; i < c->nchains; ++i)
@@ -564,6 +590,12 @@ int stash_state(hqmc_ctx *c) {
     HQMC_CUDA(c, cudaMemcpy(c->keep_bits.data(), c->st.sbits, sb * 4, cudaMemcpyDeviceToHost));
     HQMC_CUDA(c, cudaMemcpy(c->keep_x.data(), c->st.x, xb * 2, cudaMemcpyDeviceToHost));
     HQMC_CUDA(c, cudaMemcpy(&c->keep_sweep, c->st.sweep, 8, cudaMemcpyDeviceToHost));
+    size_t pb = 0;
+    for (auto &d : c->cdev) pb += 4ull * d.Nsig;
+    c->keep_perm.resize(pb);
+    c->keep_parity.resize(c->cdev.size());
+    if (pb) HQMC_CUDA(c, cudaMemcpy(c->keep_perm.data(), c->st.perm, pb * 4, cudaMemcpyDeviceToHost));
+    HQMC_CUDA(c, cudaMemcpy(c->keep_parity.data(), c->st.parity, c->keep_parity.size() * 4, cudaMemcpyDeviceToHost));
     c->keep_started = c->started;
     c->pending_restore = true;
     free_layout(c);
@@ -576,6 +608,13 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     const bool prof = !capture && c->prof_max > 0 && c->prof_n < c->prof_max;
     cudaEvent_t *pe = prof ? &c->prof_ev[4 * size_t(c->prof_n)] : nullptr;
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[0], st));
+    // permutation update at tau = beta before the FFBS of the sweep (Sec. 3.5.3)
+    if (c->perm_on) {
+        int max_pairs = 0;
+        for (auto &d : c->cdev) max_pairs = std::max(max_pairs, d.Nsig / 2);
+        cudaError_t e = launch_perm(c->st, c->nchains, max_pairs, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "perm launch");
+    }
     // fork: class k > 0 on aux stream k-1
     if (nk > 1) {
         while ((int)c->aux.size() < nk - 1) {
@@ -603,7 +642,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.class_unit_off = cls + n + (n + 1) + 1;
         fl.total_units = cl.total_units;
         fl.len_max = cl.len_max;
-        fl.blocks = cl.total_units != cl.total_pairs ? 1 : 0;
+        fl.general = (cl.total_units != cl.total_pairs || c->perm_used) ? 1 : 0;
         fl.scratch = c->base + cl.scratch_off;
         fl.slot_elems = (long long)cl.len_max * cl.L * cl.L;
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
@@ -788,6 +827,73 @@ int hqmc_set_block(hqmc_ctx *c, int chain, int B) {
     // the work-unit tables, partial sums and scratch depend on the blocks: lay the context
     // out again at its next use, keeping the state
     if (changed) return stash_state(c);
+    return HQMC_OK;
+}
+
+int hqmc_set_permutations(hqmc_ctx *c, int on) {
+    if (!c) return HQMC_ERR_ARG;
+    if (on) {
+        for (auto &h : c->ch) {
+            if (!h.set) return fail(c, HQMC_ERR_STATE, "set_params has not been called for every chain");
+            if (h.M < 2) return fail(c, HQMC_ERR_UNSUPPORTED, "permutation updates need M >= 2");
+        }
+        c->perm_used = true;
+    }
+    c->perm_on = on != 0;
+    drop_graph(c);  // the captured sweep changes
+    return HQMC_OK;
+}
+
+int hqmc_get_perm(hqmc_ctx *c, int chain, int32_t *perm, int *sign) {
+    if (!c || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    if (perm)
+        HQMC_CUDA(c, cudaMemcpyAsync(perm, c->st.perm + d.perm_off, 2ull * d.Nsig * 4, cudaMemcpyDeviceToHost, c->stream));
+    unsigned par = 0;
+    HQMC_CUDA(c, cudaMemcpyAsync(&par, c->st.parity + chain, 4, cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (sign) *sign = (par & 1u) ? -1 : 1;
+    return HQMC_OK;
+}
+
+int hqmc_set_perm(hqmc_ctx *c, int chain, const int32_t *perm) {
+    if (!c || !perm || chain < 0 || chain >= c->nchains) return HQMC_ERR_ARG;
+    int rc = prepare(c);
+    if (rc) return rc;
+    const ChainDev &d = c->cdev[chain];
+    const int Ns = d.Nsig;
+    std::vector<int> buf(4ull * Ns);
+    unsigned par = 0;
+    for (int sg = 0; sg < 2; ++sg) {
+        std::vector<char> seen(Ns, 0);
+        for (int p = 0; p < Ns; ++p) {
+            const int q = perm[sg * Ns + p];
+            if (q < 0 || q >= Ns || seen[q]) return fail(c, HQMC_ERR_ARG, "not a permutation of the worldlines");
+            seen[q] = 1;
+            buf[sg * Ns + p] = q;
+            buf[2 * Ns + sg * Ns + q] = p;
+        }
+        // parity: (length - 1) summed over the cycles
+        std::vector<char> vis(Ns, 0);
+        for (int p = 0; p < Ns; ++p) {
+            if (vis[p]) continue;
+            int len = 0;
+            for (int j = p; !vis[j]; j = perm[sg * Ns + j]) {
+                vis[j] = 1;
+                ++len;
+            }
+            par ^= unsigned(len - 1) & 1u;
+        }
+    }
+    if (Ns > 0) {
+        c->perm_used = true;
+        drop_graph(c);
+        HQMC_CUDA(c, cudaMemcpyAsync(c->st.perm + d.perm_off, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    HQMC_CUDA(c, cudaMemcpyAsync(c->st.parity + chain, &par, 4, cudaMemcpyHostToDevice, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
     return HQMC_OK;
 }
 
@@ -1026,14 +1132,18 @@ int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) 
     if (out) {
         for (int i = 0; i < c->nchains; ++i) {
             const ChainDev &d = c->cdev[i];
-            const double ns = double(acc[i].samples);
+            // sign-reweighted averages (Eq. reweight): the sums are sign-weighted and divided
+            // by the sum of signs, which equals the sample count without permutations
+            const double ns = double(acc[i].sign_sum);
             const double denom = ns * d.M * d.N;
             hqmc_obs &o = out[i];
             o.n_samples = (int64_t)acc[i].samples;
-            o.density = denom > 0 ? double(acc[i].n_sum) / denom : 0.0;
-            o.double_occ = denom > 0 ? double(acc[i].d_sum) / denom : 0.0;
-            o.m2 = denom > 0 ? double(acc[i].m2_sum) / denom : 0.0;
-            o.ekin = ns > 0 ? -(c->ch[i].t / c->ch[i].beta) * acc[i].link_sum / (ns * d.N) : 0.0;
+            o.density = denom != 0 ? double((long long)acc[i].n_sum) / denom : 0.0;
+            o.double_occ = denom != 0 ? double((long long)acc[i].d_sum) / denom : 0.0;
+            o.m2 = denom != 0 ? double((long long)acc[i].m2_sum) / denom : 0.0;
+            o.ekin = ns != 0 ? -(c->ch[i].t / c->ch[i].beta) * acc[i].link_sum / (ns * d.N) : 0.0;
+            o.mean_sign = acc[i].samples ? ns / double(acc[i].samples) : 1.0;
+            o.n_perm_accepted = (int64_t)acc[i].perm_accepted;
             const int kh = d.L / 2;
             o.s_pipi = skh[d.meas_off + kh + d.L * kh];
             o.n_degenerate = (int64_t)acc[i].degenerate;
@@ -1170,6 +1280,7 @@ int hqmc_set_checkpoint(hqmc_ctx *c, int stride, int kind) {
 
 int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_dv, double *dlogZ_dt) {
     if (!c) return HQMC_ERR_ARG;
+    if (c->perm_used) return fail(c, HQMC_ERR_UNSUPPORTED, "the adjoint is of closed loops; permutations are in use");
     int rc = prepare(c);
     if (rc) return rc;
     HQMC_CUDA(c, cudaSetDevice(c->device));

@@ -212,19 +212,26 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
                 }
                 const double v = double(re * re + im * im) / double(N);
                 if (sk_smem) skacc[o] += v;
-                else atomicAdd(&st.sk[cd.meas_off + o], v);
+                else atomicAdd(&st.sk[cd.meas_off + o], v * chain_sign(st, c));
             }
         }
         __syncthreads();
     }
     if (measure) {
+        // sums weighted by the sweep's sign sgn(P_up) sgn(P_dn) (Eq. reweight; +1 without
+        // permutations), negative contributions in two's complement
+        const int sgn = chain_sign(st, c);
+        auto wsum = [&](unsigned long long v) { return sgn > 0 ? v : 0ull - v; };
         MeasAcc &acc = st.meas[c];
-        block_add_u64(n_acc, &acc.n_sum, red);
-        block_add_u64(d_acc, &acc.d_sum, red);
-        block_add_u64(m2_acc, &acc.m2_sum, red);
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&acc.samples, 1ull);
+        block_add_u64(wsum(n_acc), &acc.n_sum, red);
+        block_add_u64(wsum(d_acc), &acc.d_sum, red);
+        block_add_u64(wsum(m2_acc), &acc.m2_sum, red);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd(&acc.samples, 1ull);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&acc.sign_sum), (unsigned long long)(long long)sgn);
+        }
         if (do_sk && sk_smem)
-            for (int k = threadIdx.x; k < N; k += blockDim.x) atomicAdd(&st.sk[cd.meas_off + k], skacc[k]);
+            for (int k = threadIdx.x; k < N; k += blockDim.x) atomicAdd(&st.sk[cd.meas_off + k], skacc[k] * sgn);
     }
 }
 
@@ -340,7 +347,8 @@ __global__ void readout_kernel(DevState st, double *cr_out, double *sk_out) {
     const int c = blockIdx.y;
     const ChainDev &cd = st.chains[c];
     const int L = cd.L, N = cd.N;
-    const unsigned long long ns = st.meas[c].samples;
+    // sign-reweighted averages: sums over the sign-weighted samples, over the sum of signs
+    const long long ns = st.meas[c].sign_sum;
     const double norm = ns ? 1.0 / (4.0 * double(ns) * cd.M) : 0.0;
     const double *sk = st.sk + cd.meas_off;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {

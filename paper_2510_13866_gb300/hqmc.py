@@ -35,6 +35,9 @@ SIGNATURES = {
     "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
     "hqmc_local_sweep": (_i, [_vp, _i]),
+    "hqmc_set_permutations": (_i, [_vp, _i]),
+    "hqmc_get_perm": (_i, [_vp, _i, _vp, _vp]),
+    "hqmc_set_perm": (_i, [_vp, _i, _vp]),
     "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
     "hqmc_set_checkpoint": (_i, [_vp, _i, _i]),
     "hqmc_log_weight_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -62,7 +65,8 @@ class HQMCError(RuntimeError):
 class Obs(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("density", C.c_double), ("double_occ", C.c_double),
                 ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double),
-                ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64), ("n_local_accepted", C.c_int64)]
+                ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64), ("n_local_accepted", C.c_int64),
+                ("mean_sign", C.c_double), ("n_perm_accepted", C.c_int64)]
 
 
 _lib = None
@@ -261,6 +265,26 @@ class Lattice:
         self.prepare()
         self._check(lib().hqmc_local_sweep(self._ctx, int(n)))
 
+    def set_permutations(self, on=True):
+        """Pair-swap permutation updates at tau = beta in every sweep (sign-reweighted
+        observables)."""
+        self._check(lib().hqmc_set_permutations(self._ctx, int(bool(on))))
+
+    def get_perm(self, chain):
+        """(perm [2, Nsig] int32 with perm[sigma, p] = P(p), sign) of one chain."""
+        self.prepare()
+        _, _, Ns = self.shapes[chain]
+        perm = np.zeros((2, Ns), dtype=np.int32)
+        sign = C.c_int(0)
+        self._check(lib().hqmc_get_perm(self._ctx, chain, _ptr(perm), C.byref(sign)))
+        return perm, sign.value
+
+    def set_perm(self, chain, perm):
+        self.prepare()
+        _, _, Ns = self.shapes[chain]
+        pa = np.ascontiguousarray(perm, dtype=np.int32).reshape(2, Ns)
+        self._check(lib().hqmc_set_perm(self._ctx, chain, _ptr(pa)))
+
     def measure(self, reset=False):
         self.prepare()
         obs = (Obs * self.n_chains)()
@@ -275,6 +299,7 @@ class Lattice:
             res.append(dict(n_samples=ob.n_samples, density=ob.density, double_occ=ob.double_occ, m2=ob.m2,
                             ekin=ob.ekin, s_pipi=ob.s_pipi, n_degenerate=ob.n_degenerate,
                             n_nonpositive=ob.n_nonpositive, n_local_accepted=ob.n_local_accepted,
+                            mean_sign=ob.mean_sign, n_perm_accepted=ob.n_perm_accepted,
                             Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
             o += N
         return res
