@@ -230,7 +230,7 @@ def workload(name, rank, chains, beta=None):
 
     if name == "L32":
         n = chains or WORK["chains"]
-        p = (WORK["t"], WORK["U"], WORK["beta"], WORK["dtau"], WORK["filling"])
+        p = (WORK["t"], WORK["U"], beta if beta else WORK["beta"], WORK["dtau"], WORK["filling"])
         return [32] * n, [p] * n, chain_seeds(rank, n)
     if name == "ragged":
         n = chains or 256
@@ -269,12 +269,15 @@ def main():
                          "(M=1024); grad16 times the adjoint")
     ap.add_argument("--local-steps", type=int, default=20,
                     help="local-update sweeps timed beside the FFBS sweep (0: skip)")
+    ap.add_argument("--conv", default="fft", choices=["fft", "stencil"],
+                    help="line convolutions of the FFBS filter (stencil: the truncated-stencil comparison)")
     ap.add_argument("--perm", action="store_true",
                     help="permutation updates at tau = beta in every sweep (sign-reweighted observables)")
     ap.add_argument("--block", type=int, default=0,
                     help="FFBS block length B (0: the closed loop from the anchor, the default)")
     ap.add_argument("--beta", type=float, default=None,
-                    help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures)")
+                    help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures), "
+                         "or of L32 in place of its beta = 4")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per GPU (default: the workload's own; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -323,6 +326,8 @@ def main():
             lt.set_block(args.block)
         if args.perm:
             lt.set_permutations(True)
+        if args.conv != "fft":
+            lt.set_conv(args.conv)
         lt.prepare()
         return lt
 
@@ -452,6 +457,10 @@ def main():
             wl += f"; block FFBS, B={args.block}"
         if args.perm:
             wl += "; permutation updates at tau = beta"
+        if args.conv != "fft":
+            wl += "; line convolutions by the periodic stencil (|d| <= 6)"
+        if args.workload == "L32" and args.beta:
+            wl += f"; beta={args.beta:g} instead (M={shapes[0][1]})"
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -210,6 +210,22 @@ int hqmc_local_sweep(hqmc_ctx *ctx, int n_sweeps);
  * Errors: HQMC_ERR_STATE (set_params missing), HQMC_ERR_UNSUPPORTED (a chain with M < 2). */
 int hqmc_set_permutations(hqmc_ctx *ctx, int on);
 
+/* Line convolutions of the FFBS forward filter (a comparison of two ways to apply the
+ * separable propagator G = g (x) g):
+ *   HQMC_CONV_FFT      half-length real FFTs with a spectral mix (the default);
+ *   HQMC_CONV_STENCIL  the direct periodic stencil out[x] = sum_{|d|<=R} g(d) v[x-d] with
+ *                      R = min(6, (L-1)/2) (and the d = L/2 term once for even L <= 12):
+ *                      the exact circulant for L <= 13, beyond it g truncated at |d| = 6,
+ *                      which drops a relative weight below 2 sum_{d>6} g(d) / sum_d g(d)
+ *                      per slice (about 3e-13 at t dtau = 0.05).  Sums of non-negative
+ *                      terms keep small filter values accurate where the FFT leaves a
+ *                      rounding floor.
+ * Applies to L <= 32 (both precisions); the adjoint keeps its FFT.
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_UNSUPPORTED (a chain with L > 32). */
+#define HQMC_CONV_FFT 0
+#define HQMC_CONV_STENCIL 1
+int hqmc_set_conv(hqmc_ctx *ctx, int kind);
+
 /* The permutations of chain c, perm [2][Nsig] (host, int32: perm[sigma][p] = P(p)), and
  * sign = sgn(P_up) sgn(P_dn); either may be NULL.  hqmc_set_perm overwrites them (each row
  * must be a permutation of 0..Nsig-1; the sign follows from the parities).

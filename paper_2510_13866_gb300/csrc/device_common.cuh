@@ -381,6 +381,33 @@ __device__ __forceinline__ void conv_line(V (&v)[L], const V *mix) {
     line_inv<L>(z, v);
 }
 
+// The same line convolution as a direct periodic stencil, out[x] = sum_d g(d) v[x - d]
+// over |d| <= R, R = min(kStencilR, (L-1)/2), with the d = L/2 term once for even
+// L <= 2 kStencilR: the exact circulant up to L = 2 kStencilR + 1, beyond it g truncated
+// at |d| = kStencilR (the comparison of a truncated separable stencil with the FFT).
+// Every output is a sum of non-negative terms for non-negative input, so small values
+// keep their relative accuracy instead of sitting on an FFT rounding floor.  g holds
+// g(0..L-1) as scalars (shared memory).  The outputs go to dst[x * stride] (shared
+// memory) as they are formed, so the input line is the only array held in registers.
+constexpr int kStencilR = 6;
+template <int L, typename V, typename T>
+__device__ __forceinline__ void stencil_store(const V (&v)[L], const T *g, V *dst, int stride) {
+    constexpr int R = ((L - 1) / 2 < kStencilR) ? (L - 1) / 2 : kStencilR;
+    constexpr bool half = (L % 2 == 0) && (L / 2 <= kStencilR);
+    V tap[R + 2];
+#pragma unroll
+    for (int d = 0; d <= R; ++d) tap[d] = vsplat(g[d]);
+    if constexpr (half) tap[R + 1] = vsplat(g[L / 2]);
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+        V acc = vmul(tap[0], v[x]);
+#pragma unroll
+        for (int d = 1; d <= R; ++d) acc = vfma(tap[d], vadd(v[(x - d + L) % L], v[(x + d) % L]), acc);
+        if constexpr (half) acc = vfma(tap[R + 1], v[(x + L / 2) % L], acc);
+        dst[x * stride] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key (seed, 0)
 // ---------------------------------------------------------------------------------

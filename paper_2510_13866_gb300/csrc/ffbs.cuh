@@ -133,11 +133,12 @@ __device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_
     else cp_async8(sdst + sc, gsrc + gc);
 }
 
+// STN: line convolutions by the periodic stencil (stencil_store) instead of the FFT.
 // BLK: the general work units -- FFBS blocks B < M and/or a permutation at tau = beta (the
 // closed-loop instantiation carries none of that bookkeeping).  With a permutation P the
 // unit of worldline p runs from slice a of p to slice a of P(p): its positions at or past
 // the wrap (a + offset >= M) are slices of worldline P(p).
-template <typename T, int L, bool BLK>
+template <typename T, int L, bool BLK, bool STN>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevState st, FfbsLaunch fl) {
     using G = FfbsGeo<T, L>;
     using V = vec2_t<T>;
@@ -286,6 +287,35 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
 #pragma unroll
                 for (int j = 0; j < L / CH; ++j) store_chunk<T, L>(dst, j * L + gl, &v[CH * j]);
             }
+            if constexpr (STN) {
+                // the lane's own row of the transpose buffer back into registers
+                auto read_row = [&]() {
+                    const V *src = xbuf + gl * LP;
+                    if constexpr (CH == 2) {
+#pragma unroll
+                        for (int j = 0; j < L / 2; ++j) {
+                            const float4 c4 = reinterpret_cast<const float4 *>(src)[j];
+                            v[2 * j] = make_float2(c4.x, c4.y);
+                            v[2 * j + 1] = make_float2(c4.z, c4.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int p = 0; p < L; ++p) v[p] = src[p];
+                    }
+                };
+                // stencil along the register direction, written straight into the transpose
+                // (lane p, register r -> lane r, register p) ...
+                __syncwarp(gmask);
+                if (active) stencil_store<L>(v, g2, xbuf + gl, LP);
+                __syncwarp(gmask);
+                if (active) {
+                    read_row();
+                    // ... and along the other direction into the lane's own row of the
+                    // transpose buffer (read only by this lane)
+                    stencil_store<L>(v, g2, xbuf + gl * LP, 1);
+                    read_row();
+                }
+            } else {
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 conv_line<L>(v, mix);
@@ -312,6 +342,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                         }
                     }
                 }
+            }
             }
             // v = alpha_{l+1} (scale 2^{-esum}) in the other layout
             V s = vzero(v[0]);

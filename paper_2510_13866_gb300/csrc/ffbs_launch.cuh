@@ -13,8 +13,13 @@ namespace hqmc {
 template <typename T, int L>
 static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
-    if (fl.general) ffbs_kernel<T, L, true><<<grid, wpc * 32, sm, s>>>(st, fl);
-    else ffbs_kernel<T, L, false><<<grid, wpc * 32, sm, s>>>(st, fl);
+    if (fl.stencil) {
+        if (fl.general) ffbs_kernel<T, L, true, true><<<grid, wpc * 32, sm, s>>>(st, fl);
+        else ffbs_kernel<T, L, false, true><<<grid, wpc * 32, sm, s>>>(st, fl);
+    } else {
+        if (fl.general) ffbs_kernel<T, L, true, false><<<grid, wpc * 32, sm, s>>>(st, fl);
+        else ffbs_kernel<T, L, false, false><<<grid, wpc * 32, sm, s>>>(st, fl);
+    }
     return cudaGetLastError();
 }
 
@@ -22,10 +27,12 @@ static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, i
 template <typename T, int L>
 static cudaError_t ffbs_occ(int wpc, int *blocks) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
-    auto kb = ffbs_kernel<T, L, true>;
-    cudaError_t e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    if (e != cudaSuccess) return e;
-    auto k = ffbs_kernel<T, L, false>;
+    cudaError_t e = cudaSuccess;
+    for (auto kx : {ffbs_kernel<T, L, true, false>, ffbs_kernel<T, L, true, true>, ffbs_kernel<T, L, false, true>}) {
+        e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+    }
+    auto k = ffbs_kernel<T, L, false, false>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     if (e != cudaSuccess) return e;
     // both instantiations are held to the same launch bounds; the closed-loop one sizes the grid

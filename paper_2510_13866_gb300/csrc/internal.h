@@ -115,6 +115,7 @@ struct FfbsLaunch {
     void *scratch;             // slots of len_max * L * L complex values
     long long slot_elems;      // complex elements per slot
     unsigned *next_unit;       // work counter: groups take units in order (zeroed per launch)
+    int stencil;               // line convolutions by the periodic stencil instead of the FFT
     int general;               // some chain has FFBS blocks B < M, or the context has used
                                // permutations: the general work-unit instantiation runs
 };

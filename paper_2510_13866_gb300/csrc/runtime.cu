@@ -85,6 +85,7 @@ struct hqmc_ctx {
     int wpc = 0;
     int slices_per_cta = 4;  // Gibbs/measure kernel: slices handled by one CTA
     bool perm_on = false;    // permutation updates at tau = beta in every sweep
+    int conv = HQMC_CONV_FFT;  // line convolutions of the FFBS: FFT or periodic stencil
     bool perm_used = false;  // a permutation other than the identity may be in the state
     int num_sms = 0;
     std::string err;
@@ -643,6 +644,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.total_units = cl.total_units;
         fl.len_max = cl.len_max;
         fl.general = (cl.total_units != cl.total_pairs || c->perm_used) ? 1 : 0;
+        fl.stencil = (c->conv == HQMC_CONV_STENCIL && !is_big(cl.L)) ? 1 : 0;
         fl.scratch = c->base + cl.scratch_off;
         fl.slot_elems = (long long)cl.len_max * cl.L * cl.L;
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
@@ -827,6 +829,16 @@ int hqmc_set_block(hqmc_ctx *c, int chain, int B) {
     // the work-unit tables, partial sums and scratch depend on the blocks: lay the context
     // out again at its next use, keeping the state
     if (changed) return stash_state(c);
+    return HQMC_OK;
+}
+
+int hqmc_set_conv(hqmc_ctx *c, int kind) {
+    if (!c || (kind != HQMC_CONV_FFT && kind != HQMC_CONV_STENCIL)) return HQMC_ERR_ARG;
+    if (kind == HQMC_CONV_STENCIL)
+        for (auto &h : c->ch)
+            if (is_big(h.L)) return fail(c, HQMC_ERR_UNSUPPORTED, "the stencil form covers L <= 32");
+    c->conv = kind;
+    drop_graph(c);
     return HQMC_OK;
 }
 

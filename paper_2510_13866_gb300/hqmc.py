@@ -36,6 +36,7 @@ SIGNATURES = {
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
     "hqmc_local_sweep": (_i, [_vp, _i]),
     "hqmc_set_permutations": (_i, [_vp, _i]),
+    "hqmc_set_conv": (_i, [_vp, _i]),
     "hqmc_get_perm": (_i, [_vp, _i, _vp, _vp]),
     "hqmc_set_perm": (_i, [_vp, _i, _vp]),
     "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
@@ -264,6 +265,10 @@ class Lattice:
         then the Gibbs step and observables)."""
         self.prepare()
         self._check(lib().hqmc_local_sweep(self._ctx, int(n)))
+
+    def set_conv(self, kind):
+        """Line convolutions of the FFBS filter: "fft" (default) or "stencil"."""
+        self._check(lib().hqmc_set_conv(self._ctx, {"fft": 0, "stencil": 1}[kind]))
 
     def set_permutations(self, on=True):
         """Pair-swap permutation updates at tau = beta in every sweep (sign-reweighted
