@@ -163,7 +163,8 @@ cudaError_t launch_perm(const DevState &st, int nchains, int max_pairs, cudaStre
 
 __device__ __forceinline__ int chain_sign(const DevState &st, int c) { return (st.parity[c] & 1u) ? -1 : 1; }
 cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStream_t stream);
+// observables read-out: S(k) and C(r) of every chain; tmp holds 2 N doubles per chain
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
-                           double *sk_out, long long total_N, cudaStream_t stream);
+                           double *sk_out, double *tmp, cudaStream_t stream);
 
 }  // namespace hqmc

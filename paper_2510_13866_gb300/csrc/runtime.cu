@@ -101,9 +101,9 @@ struct hqmc_ctx {
     std::vector<ChainDev> cdev;
     std::vector<LClass> classes;
     DevState st{};
-    size_t off_cr = 0, off_sko = 0, total_N = 0;
+    size_t off_cr = 0, off_sko = 0, off_rd = 0, total_N = 0;
     long long total_wl = 0;
-    double *d_cr = nullptr, *d_sko = nullptr;
+    double *d_cr = nullptr, *d_sko = nullptr, *d_rd = nullptr;
     uint64_t sweeps_host = 0;
 
     cudaGraph_t graph = nullptr;
@@ -395,6 +395,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     const size_t o_par = take(size_t(nc) * 4);
     c->off_cr = take(size_t(mb) * 8);
     c->off_sko = take(size_t(mb) * 8);
+    c->off_rd = take(size_t(mb) * 16);  // read-out passes: 2 N doubles per chain
     // classes
     for (auto &k : c->classes) {
         k.pair_off.assign(1, 0);
@@ -507,6 +508,7 @@ int prepare(hqmc_ctx *c) {
     s.parity = rebase(s.parity, c->base);
     c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
     c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
+    c->d_rd = reinterpret_cast<double *>(c->base + c->off_rd);
     cudaStream_t st = c->stream;
     HQMC_CUDA(c, cudaMemsetAsync(c->base, 0, need, st));
     std::vector<ChainTab> tabs(c->nchains);
@@ -996,6 +998,10 @@ int hqmc_autotune(hqmc_ctx *c, int trial_sweeps, int *n_tuned) {
             if (!rc) rc = hqmc_set_block(t, int(i), hs[i]->block);
             if (rc) break;
         }
+        // the trial runs the kernel instantiation the context itself runs
+        if (!rc) rc = hqmc_set_conv(t, c->conv);
+        if (!rc && c->perm_used) rc = hqmc_set_permutations(t, c->perm_on ? 1 : 0);
+        if (!rc && c->perm_used && !c->perm_on) t->perm_used = true;
         int best = 0;
         float best_ms = 0.f;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1132,7 +1138,7 @@ int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) 
     if (!c->ready) return fail(c, HQMC_ERR_STATE, "no state yet");
     int max_N = 0;
     for (auto &d : c->cdev) max_N = std::max(max_N, d.N);
-    cudaError_t e = launch_readout(c->st, c->nchains, max_N, c->d_cr, c->d_sko, (long long)c->total_N, c->stream);
+    cudaError_t e = launch_readout(c->st, c->nchains, max_N, c->d_cr, c->d_sko, c->d_rd, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "readout");
     std::vector<MeasAcc> acc(c->nchains);
     HQMC_CUDA(c, cudaMemcpyAsync(acc.data(), c->st.meas, sizeof(MeasAcc) * c->nchains, cudaMemcpyDeviceToHost, c->stream));

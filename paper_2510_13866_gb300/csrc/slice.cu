@@ -342,22 +342,54 @@ cudaError_t launch_advance(const DevState &st, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-// C(r) = (1/N) sum_k cos(k.r) S(k) with S(k) = sk[k] / (4 samples M) (S^z = m/2).
-__global__ void readout_kernel(DevState st, double *cr_out, double *sk_out) {
+// C(r) = (1/N) sum_k cos(k.r) S(k) with S(k) = sk[k] / (4 samples M) (S^z = m/2), by
+// separable passes (O(N L) per chain instead of O(N^2)):
+//   A[ky][rx] = sum_kx S(kx, ky) cos(2 pi kx rx / L),  B[ky][rx] = sum_kx S(kx, ky) sin(...),
+//   C(rx, ry) = (1/N) sum_ky A[ky][rx] cos(2 pi ky ry / L) - B[ky][rx] sin(2 pi ky ry / L).
+// Phases are reduced mod L before the trigonometric call, so every factor is exact to
+// rounding.  Sums are sign-reweighted (divided by the sum of signs, the sample count
+// without permutations).
+__global__ void readout_rows_kernel(DevState st, double *tmp) {
     const int c = blockIdx.y;
     const ChainDev &cd = st.chains[c];
     const int L = cd.L, N = cd.N;
-    // sign-reweighted averages: sums over the sign-weighted samples, over the sum of signs
+    const double *sk = st.sk + cd.meas_off;
+    double *A = tmp + 2 * cd.meas_off, *B = A + N;
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
+        const int rx = o % L, ky = o / L;
+        double a = 0.0, b = 0.0;
+        int ph = 0;
+        for (int kx = 0; kx < L; ++kx) {
+            double sn, cs;
+            sincospi(2.0 * double(ph) / double(L), &sn, &cs);
+            a += sk[ky * L + kx] * cs;
+            b += sk[ky * L + kx] * sn;
+            ph += rx;
+            if (ph >= L) ph -= L;
+        }
+        A[o] = a;
+        B[o] = b;
+    }
+}
+
+__global__ void readout_cols_kernel(DevState st, const double *tmp, double *cr_out, double *sk_out) {
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N;
     const long long ns = st.meas[c].sign_sum;
     const double norm = ns ? 1.0 / (4.0 * double(ns) * cd.M) : 0.0;
     const double *sk = st.sk + cd.meas_off;
+    const double *A = tmp + 2 * cd.meas_off, *B = A + N;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < N; r += gridDim.x * blockDim.x) {
         const int rx = r % L, ry = r / L;
         double acc = 0.0;
-        for (int k = 0; k < N; ++k) {
-            const int kx = k % L, ky = k / L;
-            const int ph = (kx * rx + ky * ry) % L;
-            acc += sk[k] * cospi(2.0 * double(ph) / double(L));
+        int ph = 0;
+        for (int ky = 0; ky < L; ++ky) {
+            double sn, cs;
+            sincospi(2.0 * double(ph) / double(L), &sn, &cs);
+            acc += A[ky * L + rx] * cs - B[ky * L + rx] * sn;
+            ph += ry;
+            if (ph >= L) ph -= L;
         }
         cr_out[cd.meas_off + r] = acc * norm / N;
         sk_out[cd.meas_off + r] = sk[r] * norm;
@@ -365,9 +397,10 @@ __global__ void readout_kernel(DevState st, double *cr_out, double *sk_out) {
 }
 
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out, double *sk_out,
-                           long long /*total_N*/, cudaStream_t stream) {
+                           double *tmp, cudaStream_t stream) {
     dim3 grid((max_N + 255) / 256, nchains);
-    readout_kernel<<<grid, 256, 0, stream>>>(st, cr_out, sk_out);
+    readout_rows_kernel<<<grid, 256, 0, stream>>>(st, tmp);
+    readout_cols_kernel<<<grid, 256, 0, stream>>>(st, tmp, cr_out, sk_out);
     return cudaGetLastError();
 }
 
