@@ -138,7 +138,7 @@ int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
  * the context out as described at hqmc_set_class_launch.  Errors: HQMC_ERR_ARG. */
 int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
 
-/* Slices of one chain handled by one CTA of the Gibbs/measure kernel (default 8; more
+/* Slices of one chain handled by one CTA of the Gibbs/measure kernel (default 2; more
  * slices per CTA means fewer S(k) partial sums to merge, fewer means more parallelism).
  * Results do not depend on it.  Errors: HQMC_ERR_ARG (outside 1..1024). */
 int hqmc_set_slice_launch(hqmc_ctx *ctx, int slices_per_cta);

@@ -83,7 +83,7 @@ struct hqmc_ctx {
     std::vector<cudaEvent_t> ev;
     bool use_graph = true, persistent = true;
     int wpc = 0;
-    int slices_per_cta = 4;  // Gibbs/measure kernel: slices handled by one CTA
+    int slices_per_cta = 2;  // Gibbs/measure kernel: slices handled by one CTA
     bool perm_on = false;    // permutation updates at tau = beta in every sweep
     int conv = HQMC_CONV_FFT;  // line convolutions of the FFBS: FFT or periodic stencil
     bool perm_used = false;  // a permutation other than the identity may be in the state

@@ -2,6 +2,7 @@
 // observable accumulation (Sec. 3.5.4 and Sec. 4), state initialisation, the sweep
 // counter and the observable read-out.
 #include <algorithm>
+#include <cstdint>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -148,15 +149,34 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
             }
         }
         const int nquads = cd.gauss ? 0 : (N + 3) >> 2;
+        // whole quads of 16-byte aligned counts move as one vector load and one store
+        const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(hu) | reinterpret_cast<uintptr_t>(hd)) & 15) == 0;
         for (int qd = threadIdx.x; qd < nquads; qd += blockDim.x) {
             const u64x4 w4 = philox4x64_10((uint64_t)qd, (uint64_t)l, 1, sweep, cd.seed, 0);
+            int nuq[4], ndq[4];
+            if (vec) {
+                const int4 a = reinterpret_cast<const int4 *>(hu)[qd], b = reinterpret_cast<const int4 *>(hd)[qd];
+                reinterpret_cast<int4 *>(hu)[qd] = make_int4(0, 0, 0, 0);
+                reinterpret_cast<int4 *>(hd)[qd] = make_int4(0, 0, 0, 0);
+                nuq[0] = a.x; nuq[1] = a.y; nuq[2] = a.z; nuq[3] = a.w;
+                ndq[0] = b.x; ndq[1] = b.y; ndq[2] = b.z; ndq[3] = b.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int x = 4 * qd + j;
+                    nuq[j] = x < N ? hu[x] : 0;
+                    ndq[j] = x < N ? hd[x] : 0;
+                    if (x < N) {
+                        hu[x] = 0;
+                        hd[x] = 0;
+                    }
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int x = 4 * qd + j;
                 if (x >= N) break;
-                const int nu = hu[x], nd = hd[x];
-                hu[x] = 0;
-                hd[x] = 0;
+                const int nu = nuq[j], nd = ndq[j];
                 const int m = nu - nd;
                 const double pplus = (m >= -kPTab && m <= kPTab) ? tb.pplus[m + kPTab]
                                                                   : 1.0 / (1.0 + exp(-2.0 * lam * m));
