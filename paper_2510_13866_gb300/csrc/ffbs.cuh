@@ -484,20 +484,24 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             __syncwarp(gmask);
             if (i > 1) prefetch(i - 1);
 
-            // uniforms of this slice for both worldlines (lanes 0 and 1 compute, then share)
-            const int grp = lb >> 2;
-            if (grp != cached) {
-                const u64x4 w4 = philox4x64_10((uint64_t)grp, (gl & 1) ? wl1 : wl0, 0, sweep, cd.seed, 0);
+            // uniforms of this slice for both worldlines: one Philox call per lane fills the
+            // words of GW/2 groups of four slices at once (lane 2k + w: group k of the block,
+            // worldline w), then the slice's two words are shared from their lanes
+            constexpr int PG = GW / 2;
+            const int grp = lb >> 2, blk = grp / PG;
+            if (blk != cached) {
+                const u64x4 w4 = philox4x64_10((uint64_t)(blk * PG + (gl >> 1)), (gl & 1) ? wl1 : wl0, 0, sweep,
+                                               cd.seed, 0);
                 wd0 = w4.v[0];
                 wd1 = w4.v[1];
                 wd2 = w4.v[2];
                 wd3 = w4.v[3];
-                cached = grp;
+                cached = blk;
             }
-            const int wsel = lb & 3;
+            const int wsel = lb & 3, src = 2 * (grp - blk * PG);
             const uint64_t myw = wsel == 0 ? wd0 : wsel == 1 ? wd1 : wsel == 2 ? wd2 : wd3;
-            const uint64_t uw0 = __shfl_sync(gmask, myw, 0, GW);
-            const uint64_t uw1 = __shfl_sync(gmask, myw, 1, GW);
+            const uint64_t uw0 = __shfl_sync(gmask, myw, src, GW);
+            const uint64_t uw1 = __shfl_sync(gmask, myw, src + 1, GW);
 
             // p(y) = max(f, 0) g(ix - cx) g(iy - cy): x-weights shared through wx
             const int cx0 = cur0 % L, cy0 = cur0 / L, cx1 = cur1 % L, cy1 = cur1 / L;
