@@ -442,18 +442,22 @@ __global__ void __launch_bounds__(BigGeo<L>::NT, BigGeo<L>::MINB) ffbs_big_kerne
                     for (int e = 0; e < E; ++e) f[e] = src[(hb * E + e) * 2];
                 }
             }
-            // uniforms of this slice (threads 0 and 1), x-weights of both worldlines
-            const int grp = lb >> 2;
-            if (tid < 2 && grp != cached) {
-                const u64x4 w4 = philox4x64_10((uint64_t)grp, tid ? wl1 : wl0, 0, sweep, cd.seed, 0);
+            // uniforms of this slice: the first warp's 32 threads fill the words of 16 groups
+            // of four slices at once (thread 2k + w: group k of the block, worldline w); the
+            // slice's two threads publish theirs.  Then the x-weights of both worldlines.
+            constexpr int PG = 16;
+            const int grp = lb >> 2, blk = grp / PG;
+            if (tid < 2 * PG && blk != cached) {
+                const u64x4 w4 = philox4x64_10((uint64_t)(blk * PG + (tid >> 1)), (tid & 1) ? wl1 : wl0, 0, sweep,
+                                               cd.seed, 0);
                 wd0 = w4.v[0];
                 wd1 = w4.v[1];
                 wd2 = w4.v[2];
                 wd3 = w4.v[3];
-                cached = grp;
+                cached = blk;
             }
-            const int wsel = lb & 3;
-            if (tid < 2) ubuf[tid] = wsel == 0 ? wd0 : wsel == 1 ? wd1 : wsel == 2 ? wd2 : wd3;
+            const int wsel = lb & 3, src = 2 * (grp - blk * PG);
+            if (tid >= src && tid < src + 2) ubuf[tid - src] = wsel == 0 ? wd0 : wsel == 1 ? wd1 : wsel == 2 ? wd2 : wd3;
             const int cx0 = cur0 % L, cy0 = cur0 / L, cx1 = cur1 % L, cy1 = cur1 / L;
             __syncthreads();
             if (i > 1) prefetch(i - 1);
