@@ -199,10 +199,13 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
             srow_g[(long long)l * L * wpl + k] = rows[k];
             scol_g[(long long)l * L * wpl + k] = cols[k];
         }
+        // S(k) of a real field: m^(-k) = conj(m^(k)), so only kx = 0..L/2 is transformed and
+        // |m^(L - kx, L - ky)|^2 = |m^(kx, ky)|^2 fills the other half
+        const int K1 = L / 2 + 1;  // kx = 0 .. L/2
         if (do_sk) {
             // x1[iy][kx] = sum_ix m[iy][ix] e^{-2 pi i kx ix / L}
-            for (int o = threadIdx.x; o < N; o += blockDim.x) {
-                const int kx = o % L, iy = o / L;
+            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
+                const int kx = o % K1, iy = o / K1;
                 float re = 0.f, im = 0.f;
                 int ph = 0;
                 for (int ix = 0; ix < L; ++ix) {
@@ -219,20 +222,28 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
         for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
         if (do_sk) {
             // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N
-            for (int o = threadIdx.x; o < N; o += blockDim.x) {
-                const int kx = o % L, ky = o / L;
+            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
+                const int kx = o % K1, ky = o / K1;
                 float re = 0.f, im = 0.f;
                 int ph = 0;
                 for (int iy = 0; iy < L; ++iy) {
-                    const float2 a = x1[iy * L + kx], w = tw[ph];
+                    const float2 a = x1[iy * K1 + kx], w = tw[ph];
                     re += a.x * w.x - a.y * w.y;
                     im += a.x * w.y + a.y * w.x;
                     ph += ky;
                     if (ph >= L) ph -= L;
                 }
                 const double v = double(re * re + im * im) / double(N);
-                if (sk_smem) skacc[o] += v;
-                else atomicAdd(&st.sk[cd.meas_off + o], v * chain_sign(st, c));
+                const int k = ky * L + kx;
+                const bool mirror = kx > 0 && 2 * kx < L;
+                const int km = (ky == 0 ? 0 : L - ky) * L + (L - kx);
+                if (sk_smem) {
+                    skacc[k] += v;
+                    if (mirror) skacc[km] += v;
+                } else {
+                    atomicAdd(&st.sk[cd.meas_off + k], v * chain_sign(st, c));
+                    if (mirror) atomicAdd(&st.sk[cd.meas_off + km], v * chain_sign(st, c));
+                }
             }
         }
         __syncthreads();
