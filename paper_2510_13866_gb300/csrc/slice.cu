@@ -31,7 +31,7 @@ __device__ void block_add_u64(unsigned long long v, unsigned long long *dst, uns
 }
 
 struct SliceSmem {
-    size_t rows, red, ms, x1, tw, sk, total;
+    size_t rows, red, pp, ms, x1, tw, sk, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -42,7 +42,8 @@ __host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl) {
     SliceSmem s{};
     s.rows = 0;
     s.red = align16(s.rows + 2 * size_t(L) * wpl * 4);
-    s.ms = align16(s.red + 32 * 8);
+    s.pp = align16(s.red + 32 * 8);
+    s.ms = align16(s.pp + (2 * kPTab + 1) * 8);
     s.x1 = align16(s.ms + N * 4);
     s.tw = align16(s.x1 + N * 8);
     s.sk = align16(s.tw + size_t(L) * 8);
@@ -99,12 +100,14 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
     uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
     uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
+    double *pp = reinterpret_cast<double *>(smem_raw + lay.pp);         // P(s=+1 | m), |m| <= kPTab
     float *ms = reinterpret_cast<float *>(smem_raw + lay.ms);            // [N] m of the slice
     float2 *x1 = reinterpret_cast<float2 *>(smem_raw + lay.x1);          // [N] row DFT
     float2 *tw = reinterpret_cast<float2 *>(smem_raw + lay.tw);          // [L] e^{-2 pi i j / L}
     double *skacc = reinterpret_cast<double *>(smem_raw + lay.sk);       // [N]
 
     for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+    for (int k = threadIdx.x; k < 2 * kPTab + 1; k += blockDim.x) pp[k] = tb.pplus[k];
     if (do_sk) {
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
             float s, co;
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
                 if (x >= N) break;
                 const int nu = nuq[j], nd = ndq[j];
                 const int m = nu - nd;
-                const double pplus = (m >= -kPTab && m <= kPTab) ? tb.pplus[m + kPTab]
+                const double pplus = (m >= -kPTab && m <= kPTab) ? pp[m + kPTab]
                                                                   : 1.0 / (1.0 + exp(-2.0 * lam * m));
                 const bool up = u53(w4.v[j]) < pplus;
                 const int ix = x % L, iy = x / L;
