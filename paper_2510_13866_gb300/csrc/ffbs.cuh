@@ -281,6 +281,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         T fin0 = T(0), fin1 = T(0);
         int l = l0;
         for (int i = 0; i < len; ++i) {
+            // the next slice's field bits (Hirsch chains), loaded before this slice's
+            // convolutions so that their latency is hidden behind them
+            uint32_t wnext = 0u;
+            if (!cd.gauss && active && i < len - 1) {
+                const int ln1 = (l + 1 == M) ? 0 : l + 1;
+                wnext = ((i & 1) ? srow : scol)[((long long)ln1 * L + gl) * cd.wpl];
+            }
             // f_l of slice i, in the writer's layout: chunk j*L + lane holds registers CH*j..
             if (i >= 1 && active) {
                 V *dst = slot + (long long)i * N;
@@ -374,8 +381,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 if (cd.gauss) {
                     if (active) mul_gauss_line<T, L>(v, gauss_line<T>(st, cd, (i & 1) == 0, l1, gl), sc0, sc1);
                 } else {
-                    const uint32_t *wsrc = (i & 1) ? srow : scol;
-                    const uint32_t w = active ? wsrc[((long long)l1 * L + gl) * cd.wpl] : 0u;
+                    const uint32_t w = wnext;
 #pragma unroll
                     for (int r = 0; r < L; ++r) v[r] = vmul(v[r], ((w >> r) & 1u) ? A : B);
                 }
