@@ -43,7 +43,8 @@ struct FfbsGeo {
     static constexpr size_t WXB = a16(size_t(L) * sizeof(V));
     static constexpr size_t RBB = a16(size_t(2 * L) * sizeof(V));  // crossing rows of both worldlines
     static constexpr size_t METAB = 32;  // the work unit's block bookkeeping
-    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB + RBB + METAB;
+    static constexpr size_t HLB = a16(size_t(L) * sizeof(float));  // link table d/dt log g
+    static constexpr size_t GROUP_BYTES = XBUF + MIXB + G2B + WXB + RBB + METAB + HLB;
 };
 
 // Target u*S of an inverse-CDF draw from the Philox word w, in the CDF's precision.
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
     // wrap, successors of both worldlines), parked in shared memory across the forward loop
     // instead of in registers
     volatile int *meta = reinterpret_cast<volatile int *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB + G::RBB);
+    float *hsm = reinterpret_cast<float *>(gsm + G::XBUF + G::MIXB + G::G2B + G::WXB + G::RBB + G::METAB);
     const long long gid = ((long long)blockIdx.x * wpc + warp) * G::GPW + gw;
     const long long ngroups = (long long)gridDim.x * wpc * G::GPW;
     V *slot = reinterpret_cast<V *>(fl.scratch) + gid * fl.slot_elems;
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             for (int j = gl; j < L; j += GW) mix[j] = vsplat(src[j]);
             const T *gs = tab_g<T>(tb);
             for (int j = gl; j < 2 * L; j += GW) g2[j] = gs[j < L ? j : j - L];
+            for (int j = gl; j < L; j += GW) hsm[j] = tb.h_f[j];
         }
         __syncwarp(gmask);
 
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         };
         __syncwarp(gmask);
         if (len > 1) prefetch(len - 1);
-        const float *hl = tb.h_f;
+        const float *hl = hsm;  // the link sums read the table from shared memory
         int *hist_s = st.hist + cd.h_off + (long long)sg * M * N;
         float ek0 = 0.f, ek1 = 0.f;
         const int le = end_slice();
