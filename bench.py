@@ -245,6 +245,33 @@ def workload(name, rank, chains, beta=None):
     return [L] * n, [(1.0, 4.0, beta if beta else 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
 
 
+def same_accuracy(make, lat64, sweeps):
+    """The FP32 filter against the plain FP64 form at equal work: FP32 chains with the
+    FP64 chains' seeds run the same number of sweeps from the same start.  Both chains of
+    a seed then share their paths until a uniform falls within FP32 rounding of a CDF
+    edge, so each observable's FP32 - FP64 difference is set against the FP64 estimate's
+    statistical error over the independent chains (equal accuracy: |diff| well below it)."""
+    import numpy as np
+
+    lat32 = make("fp32")
+    lat32.sweep(sweeps)
+    obs32, obs64 = lat32.measure(), lat64.measure()
+    same = sum(np.array_equal(lat32.get_state(c)[1], lat64.get_state(c)[1]) for c in range(len(obs64)))
+    lat32.close()
+    names = ("double_occ", "m2", "ekin", "s_pipi")
+    a = np.array([[o[k] for k in names] for o in obs32])
+    b = np.array([[o[k] for k in names] for o in obs64])
+    n = len(b)
+    se = b.std(axis=0, ddof=1) / np.sqrt(n) if n > 1 else np.full(len(names), np.nan)
+    out = {"sweeps": sweeps, "chains": n, "chains_with_identical_paths": int(same), "observables": {}}
+    for j, k in enumerate(names):
+        d = float(a[:, j].mean() - b[:, j].mean())
+        out["observables"][k] = {"fp32": float(a[:, j].mean()), "fp64": float(b[:, j].mean()),
+                                 "fp64_stat_err": float(se[j]), "diff": d,
+                                 "diff_over_stat_err": d / float(se[j]) if se[j] > 0 else None}
+    return out
+
+
 def kernel_source_digest():
     """Digest of the FFBS kernel sources: the committed DRAM counters apply only to it."""
     import hashlib
@@ -441,6 +468,7 @@ def main():
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         v64 = world * args.fp64_steps / (ms64 / 1e3)
         fp64 = {"value": v64, "unit": "sweeps/s", "steps": args.fp64_steps, "fp32_over_fp64": value / v64}
+        fp64["accuracy"] = same_accuracy(make, lat64, 1 + args.fp64_steps)
         lat64.close()
 
     cpu = None
