@@ -337,6 +337,15 @@ int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, double dtau, u
                       uint64_t sweep, const int8_t *s, int32_t *x, double *logw, int precision,
                       void *stream);
 
+/* Measured FP32 fused multiply-add throughput of GPU `device` in TFLOP/s, written to
+ * *tflops (host): the denominator of the FFBS kernels' ALU roofline.  packed = 1 times the
+ * packed f32x2 instruction (FFMA2, 4 flops) that the line FFTs use, packed = 0 the scalar
+ * FFMA (2 flops).  One wave of CTAs on every SM runs independent FMA chains; the best of
+ * five timed launches counts.  Takes a few ms; allocates and frees a small buffer and a
+ * stream of its own, and restores the current device.  Errors: HQMC_ERR_ARG (null
+ * pointer, packed not 0 or 1), HQMC_ERR_CUDA. */
+int hqmc_fp32_peak(int device, int packed, double *tflops);
+
 /* Lattice sizes built into this library: writes up to cap entries, returns the count. */
 int hqmc_supported_L(int *out, int cap);
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "hqmc_profile_read": (_i, [_vp, _vp, _vp, _vp]),
     "hqmc_ffbs_noalloc": (_i, [_i, _i, _i, _d, _d, _d, _u64, _u64, _vp, _vp, _vp, _i, _vp]),
     "hqmc_supported_L": (_i, [_vp, _i]),
+    "hqmc_fp32_peak": (_i, [_i, _i, C.POINTER(_d)]),
     "hqmc_destroy": (None, [_vp]),
     "hqmc_strerror": (C.c_char_p, [_i]),
     "hqmc_last_error_detail": (C.c_char_p, [_vp]),
@@ -93,6 +94,16 @@ def supported_L():
     buf = (C.c_int * n)()
     lib().hqmc_supported_L(buf, n)
     return list(buf)
+
+
+def fp32_peak(device=0, packed=True):
+    """Measured FP32 fused multiply-add throughput (TFLOP/s) of `device`: packed f32x2
+    (FFMA2, as the line FFTs run) or scalar FFMA."""
+    out = C.c_double(0.0)
+    rc = lib().hqmc_fp32_peak(int(device), int(bool(packed)), C.byref(out))
+    if rc != 0:
+        raise HQMCError(rc, "hqmc_fp32_peak")
+    return out.value
 
 
 def _ptr(a):

@@ -65,6 +65,9 @@ def test_init_rejects_bad_arguments_without_a_gpu(libpath):
     L[0] = 4
     assert lib.hqmc_init_lattice(ctypes.byref(ctx), 0, L, seeds, 0, 0) == -1
     assert lib.hqmc_init_lattice(ctypes.byref(ctx), 1, L, seeds, 7, 0) == -1
+    out = ctypes.c_double(1.0)
+    assert lib.hqmc_fp32_peak(0, 2, ctypes.byref(out)) == -1 and out.value == 1.0
+    assert lib.hqmc_fp32_peak(0, 1, None) == -1
 
 
 def test_product_path_does_not_reference_the_oracle():
