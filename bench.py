@@ -285,12 +285,15 @@ def same_accuracy(make, lat64, sweeps):
     return out
 
 
-def kernel_source_digest():
-    """Digest of the FFBS kernel sources: the committed DRAM counters apply only to it."""
+def kernel_source_digest(workload="L32"):
+    """Digest of the sources the workload's FFBS kernels compile from (the warp kernel for
+    L <= 32, the wide kernel too otherwise): the committed DRAM counters apply only to them."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("ffbs.cuh", "ffbs_big.cuh", "device_common.cuh"):
+    files = ("ffbs.cuh", "device_common.cuh") if workload == "L32" else ("ffbs.cuh", "ffbs_big.cuh",
+                                                                          "device_common.cuh")
+    for f in files:
         with open(os.path.join(ROOT, "paper_2510_13866_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -417,7 +420,7 @@ def main():
     if os.path.exists(tp):
         try:
             rec = json.load(open(tp)).get(args.workload)
-            if rec and rec.get("kernel_digest") == kernel_source_digest():
+            if rec and rec.get("kernel_digest") == kernel_source_digest(args.workload):
                 traffic = rec["bytes_per_launch"] * (nchains / rec["chains"])
                 traffic_note = rec["how"]
             elif rec:
