@@ -197,7 +197,7 @@ def test_permutation_observables_agree_statistically():
     """Sign-reweighted observables and the mean sign with pair-swap permutation updates
     (Sec. 3.5.3): FP32, FP64 and the oracle agree.  L=6 with two worldlines per spin at
     beta=0.5, where swaps are frequent (0.3 per sweep) and the mean sign is about 0.6."""
-    L, params, n_gpu, n_orc, burn, meas = 6, (1.0, 4.0, 0.5, 0.1, 1.0 / 9.0), 1024, 48, 100, 400
+    L, params, n_gpu, n_orc, burn, meas = 6, (1.0, 4.0, 0.5, 0.1, 1.0 / 9.0), 1024, 128, 100, 400
     sides = {}
     for prec, base in (("fp32", 80_000), ("fp64", 90_000)):
         num, den = gpu_side(L, params, prec, range(base, base + n_gpu), burn, meas, perm=True, signed=True)
