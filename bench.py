@@ -484,6 +484,17 @@ def main():
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         v64 = world * args.fp64_steps / (ms64 / 1e3)
         fp64 = {"value": v64, "unit": "sweeps/s", "steps": args.fp64_steps, "fp32_over_fp64": value / v64}
+        # the FP64 form's own ALU roofline: the same algorithmic flops per sweep against
+        # the measured DFMA rate (it runs the same FFTs in double)
+        try:
+            from paper_2510_13866_gb300 import fp64_peak
+
+            p64 = fp64_peak(local)
+            a64 = alg_flops / (ms64 / args.fp64_steps / 1e3) / 1e12
+            fp64["alu"] = {"achieved_tflops": a64, "peak_tflops": p64, "frac": a64 / p64,
+                           "peak_source": "measured in this run: DFMA loop on every SM"}
+        except Exception as e:  # noqa: BLE001 -- the rate stands without its roofline
+            fp64["alu"] = {"error": str(e)}
         fp64["accuracy"] = same_accuracy(make, lat64, 1 + args.fp64_steps)
         lat64.close()
 

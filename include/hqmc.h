@@ -346,6 +346,12 @@ int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, double dtau, u
  * pointer, packed not 0 or 1), HQMC_ERR_CUDA. */
 int hqmc_fp32_peak(int device, int packed, double *tflops);
 
+/* Measured FP64 fused multiply-add throughput of GPU `device` in TFLOP/s (DFMA, 2 flops),
+ * written to *tflops (host): the denominator of the plain FP64 form's ALU roofline.  Same
+ * loop structure, launch and ownership as hqmc_fp32_peak.  Errors: HQMC_ERR_ARG (null
+ * pointer), HQMC_ERR_CUDA. */
+int hqmc_fp64_peak(int device, double *tflops);
+
 /* Lattice sizes built into this library: writes up to cap entries, returns the count. */
 int hqmc_supported_L(int *out, int cap);
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "hqmc_ffbs_noalloc": (_i, [_i, _i, _i, _d, _d, _d, _u64, _u64, _vp, _vp, _vp, _i, _vp]),
     "hqmc_supported_L": (_i, [_vp, _i]),
     "hqmc_fp32_peak": (_i, [_i, _i, C.POINTER(_d)]),
+    "hqmc_fp64_peak": (_i, [_i, C.POINTER(_d)]),
     "hqmc_destroy": (None, [_vp]),
     "hqmc_strerror": (C.c_char_p, [_i]),
     "hqmc_last_error_detail": (C.c_char_p, [_vp]),
@@ -103,6 +104,15 @@ def fp32_peak(device=0, packed=True):
     rc = lib().hqmc_fp32_peak(int(device), int(bool(packed)), C.byref(out))
     if rc != 0:
         raise HQMCError(rc, "hqmc_fp32_peak")
+    return out.value
+
+
+def fp64_peak(device=0):
+    """Measured FP64 fused multiply-add throughput (TFLOP/s) of `device`."""
+    out = C.c_double(0.0)
+    rc = lib().hqmc_fp64_peak(int(device), C.byref(out))
+    if rc != 0:
+        raise HQMCError(rc, "hqmc_fp64_peak")
     return out.value
 
 

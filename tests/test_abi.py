@@ -68,6 +68,7 @@ def test_init_rejects_bad_arguments_without_a_gpu(libpath):
     out = ctypes.c_double(1.0)
     assert lib.hqmc_fp32_peak(0, 2, ctypes.byref(out)) == -1 and out.value == 1.0
     assert lib.hqmc_fp32_peak(0, 1, None) == -1
+    assert lib.hqmc_fp64_peak(0, None) == -1
 
 
 def test_product_path_does_not_reference_the_oracle():
