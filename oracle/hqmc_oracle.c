@@ -9,7 +9,8 @@
  * or calls it, and it shares no code, header or table generator with the CUDA
  * library: every table below is computed here from its definition.
  *
- * Conventions (one line each; the readings of the paper are listed in the design doc):
+ * Conventions (one line each; where the paper is silent or garbled, each states the
+ * reading taken):
  *   site index      x = ix + L*iy on an L x L torus, N = L*L.
  *   slices          l = 0..M-1, M = beta/dtau; a worldline closes: x_M == x_0 (Sec. 3.1).
  *   propagator      g(d) = (1/L) sum_j exp(2 t dtau cos(2 pi j/L)) cos(2 pi j d/L),
