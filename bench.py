@@ -83,19 +83,21 @@ def stop_clocks(proc, f, path, device):
 
 def cpu_oracle_sample(target_s=12.0):
     """Time the FP64 oracle (OpenMP over worldlines) on the first k worldlines of each
-    spin of chain 0 for one sweep; extrapolate to the whole 64-chain batch."""
+    spin of chain 0 for one sweep, k sized for about target_s seconds after an untimed
+    warm-up sweep; extrapolate per worldline to the whole 64-chain batch."""
     import oracle
 
     w = WORK
-    orc = oracle.Chain(w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
+    args = (w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
     cores = oracle.num_threads()
-    k = max(1, cores // 2)
+    k = max(1, cores // 2)  # 2k worldlines: one per thread
+    oracle.Chain(*args).sweep(nwl_limit=k)  # library load, thread pool start
+    orc = oracle.Chain(*args)
     t0 = time.perf_counter()
     orc.sweep(nwl_limit=k)
     dt = time.perf_counter() - t0
-    k2 = max(k, min(orc.Nsig, int(k * target_s / max(dt, 1e-3))))
-    k2 = (k2 + cores - 1) // cores * cores // 2 or k
-    orc2 = oracle.Chain(w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
+    k2 = max(k, min(orc.Nsig, int(k * target_s / max(dt, 1e-3)) // k * k))
+    orc2 = oracle.Chain(*args)
     t0 = time.perf_counter()
     orc2.sweep(nwl_limit=k2)
     dt2 = time.perf_counter() - t0
