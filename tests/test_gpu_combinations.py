@@ -1,0 +1,118 @@
+"""Seeded random combinations of the sweep's options against the FP64 oracle, through the
+C ABI: lattice size (warp and wide kernels), worldline count, number of slices, U of
+either sign (Hirsch or Gaussian field), FFBS blocks, permutation updates, the stencil
+convolution, precision, and ragged batches mixing all of these per chain.
+
+Every case runs two sweeps on the GPU and in the oracle from the same seeds.  Per chain:
+the anchor, the permutation and its sign, the filter log-weights (1e-5 relative in FP32,
+1e-12 in FP64), and the worldlines in draw order, which must agree up to a first
+difference at a draw whose uniform lies within the tolerance of a CDF edge; after a
+sweep with no such difference the fields must agree as well.  A chain stops being
+compared after its first difference, since the two samplers then follow different paths.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import path_mismatches, rel_err
+from test_gpu_perm import unit_mismatches
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "fp64": 1e-12}
+SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32, 48)
+
+
+def draw_cases(n=24, seed=2510):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        chains = []
+        for _ in range(3 if k % 4 == 3 else 1):
+            L = int(rng.choice(SIZES))
+            N = L * L
+            big = L >= 24  # the oracle's direct convolution costs N^2 per slice
+            nsig = int(rng.integers(1, (8 if big else N) + 1))
+            dtau = float(rng.choice([0.05, 0.1, 0.125, 0.2, 0.25]))
+            M = int(rng.integers(1, (10 if big else 24) + 1))
+            U = float(rng.choice([-4.0, 2.0, 4.0, 8.0]))
+            block = int(rng.integers(1, M + 1)) if rng.random() < 0.4 else 0
+            chains.append((L, (1.0, U, M * dtau, dtau, 2.0 * nsig / N), block))
+        perm = bool(rng.random() < 0.35)
+        prec = "fp64" if rng.random() < 0.4 and all(c[0] <= 32 for c in chains) else "fp32"
+        # the stencil (|d| <= 6) is the exact circulant for L <= 13 and is not built for
+        # the wide kernel
+        stencil = bool(rng.random() < 0.25 and all(c[0] <= 12 for c in chains))
+        out.append((chains, perm, prec, stencil))
+    return out
+
+
+CASES = draw_cases()
+
+
+def case_id(case):
+    chains, perm, prec, stencil = case
+    parts = [f"L{L}M{round(p[2] / p[3])}n{round(p[4] * L * L / 2)}U{p[1]:g}" + (f"B{b}" if b else "")
+             for L, p, b in chains]
+    return "-".join(parts) + ("-perm" if perm else "") + f"-{prec}" + ("-stencil" if stencil else "")
+
+
+@pytest.mark.parametrize("case", CASES, ids=[case_id(c) for c in CASES])
+def test_random_combination_matches_oracle(case):
+    from paper_2510_13866_gb300 import HQMCError, Lattice
+
+    chains, perm, prec, stencil = case
+    tol = TOL[prec]
+    seeds = [101 + 7 * c for c in range(len(chains))]
+    lat = Lattice([c[0] for c in chains], seeds, precision=prec)
+    for c, (L, params, block) in enumerate(chains):
+        lat.set_params(*params, chain=c)
+        if block:
+            lat.set_block(block, chain=c)
+    if stencil:
+        lat.set_conv("stencil")
+    if perm and min(round(p[2] / p[3]) for _, p, _ in chains) < 2:
+        # documented: a swap at tau = beta needs two distinct slices around it
+        with pytest.raises(HQMCError) as err:
+            lat.set_permutations(True)
+            lat.sweep(1)
+        assert err.value.code == -6  # HQMC_ERR_UNSUPPORTED
+        lat.close()
+        return
+    if perm:
+        lat.set_permutations(True)
+    orcs = [oracle.Chain(L, *params, sd) for (L, params, _), sd in zip(chains, seeds)]
+    live = [True] * len(chains)
+    for k in range(2):
+        logw = lat.sweep(1, logw=True)
+        for c, ((L, params, block), orc) in enumerate(zip(chains, orcs)):
+            if not live[c]:
+                continue
+            if perm:
+                ref = orc.perm_sweep(want_margin=True, block=block)
+                p_gpu, sign = lat.get_perm(c)
+                if not np.array_equal(p_gpu, orc.perm):
+                    # a swap decision within 1e-12 of its acceptance ratio
+                    assert np.any(ref["margin_perm"] < 1e-12), (k, c)
+                    live[c] = False
+                    continue
+                assert sign == orc.sign, (k, c)
+            else:
+                ref = orc.sweep(want_margin=True, block=block)
+            s, x, a, sw = lat.get_state(c)
+            assert sw == k + 1 and a == ref["anchor"], (k, c)
+            err = rel_err(logw[c], ref["logw"]).max()
+            assert err <= tol, (k, c, err)
+            if perm:
+                firsts, bad = unit_mismatches(x, orc.x, ref["margin"], a, orc.M, orc.perm, tol, block)
+            else:
+                _, firsts, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, tol, block=block)
+            assert not bad, (k, c, bad[:3])
+            if firsts:
+                live[c] = False
+                continue
+            if orc.gauss:
+                assert np.allclose(lat.get_sigma(c), orc.sigma, rtol=0, atol=1e-12), (k, c)
+            else:
+                assert np.array_equal(s, orc.s), (k, c)
+    lat.close()
