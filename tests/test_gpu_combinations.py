@@ -1,4 +1,4 @@
-"""Seeded random combinations of the sweep's options against the FP64 oracle, through the
+"""48 seeded random combinations of the sweep's options against the FP64 oracle, through the
 C ABI: lattice size (warp and wide kernels), worldline count, number of slices, U of
 either sign (Hirsch or Gaussian field), FFBS blocks, permutation updates, the stencil
 convolution, precision, and ragged batches mixing all of these per chain.
@@ -23,7 +23,7 @@ TOL = {"fp32": 1e-5, "fp64": 1e-12}
 SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32, 48)
 
 
-def draw_cases(n=24, seed=2510):
+def draw_cases(n=48, seed=2510):
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
