@@ -9,6 +9,14 @@ the anchor, the permutation and its sign, the filter log-weights (1e-5 relative 
 difference at a draw whose uniform lies within the tolerance of a CDF edge; after a
 sweep with no such difference the fields must agree as well.  A chain stops being
 compared after its first difference, since the two samplers then follow different paths.
+
+The FFT convolution resolves a message only to about eps log2(N) of its largest value
+(eps = 2^-24 in FP32, 2^-53 in FP64), so the log-weight of a unit whose end site carries
+a small share of the final message, kappa = max_y alpha(y) / alpha(x_end), is known only
+to about eps kappa per block.  Strong Gaussian fields (U < 0 with large |U| dtau) reach
+kappa = 1e4 to 1e15 within two sweeps.  A log-weight beyond the plain tolerance is
+therefore accepted up to tol + 4 eps log2(N) M kappa, with kappa summed over the unit's
+blocks and computed by the oracle's filter from the fields of that sweep.
 """
 import numpy as np
 import pytest
@@ -20,6 +28,7 @@ from test_gpu_perm import unit_mismatches
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-5, "fp64": 1e-12}
+EPS = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
 SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32, 48)
 
 
@@ -48,6 +57,37 @@ def draw_cases(n=48, seed=2510):
 
 
 CASES = draw_cases()
+
+
+def slice_potentials(orc):
+    """W [2][M][N] of the oracle chain's current fields (Hirsch: exp(+-lambda s) by spin;
+    Gaussian: exp(a sigma) for both spins)."""
+    if orc.gauss:
+        w = np.exp(oracle.gauss_coupling(orc.U, orc.dtau) * orc.sigma)
+        return np.stack([w, w])
+    lam = oracle.lam(orc.U, orc.dtau)
+    return np.stack([np.exp(lam * orc.s), np.exp(-lam * orc.s)])
+
+
+def unit_kappa(orc, W, a, block, sg, p):
+    """Sum over the blocks of worldline p's unit of max_y alpha_end(y) / alpha_end(x_end),
+    with the held sites read from the chain after the sweep (they do not move)."""
+    L, M, N = orc.L, orc.M, orc.N
+    g, _ = oracle.g_table(L, orc.t, orc.dtau)
+    G = np.fft.fft2(np.outer(g, g))
+    q = orc.perm[sg, p]
+    vp = np.where(np.arange(M) < a, orc.x[sg, q], orc.x[sg, p])
+    vp[a] = orc.x[sg, q, a]
+    B = block if 0 < block < M else M
+    kap = 0.0
+    for b in range(0, M, B):
+        l0, ln = (a + b) % M, min(B, M - b)
+        xs = orc.x[sg, p, a] if b == 0 else vp[l0]
+        xe = vp[(l0 + ln) % M]
+        _, f = oracle.filter_block(L, M, g, W[sg], l0, ln, int(xs), int(xe), want_f=True)
+        al = np.real(np.fft.ifft2(np.fft.fft2(f[(l0 + ln - 1) % M].reshape(L, L)) * G)).reshape(-1)
+        kap += al.max() / max(al[xe], 1e-300)
+    return kap
 
 
 def case_id(case):
@@ -88,6 +128,7 @@ def test_random_combination_matches_oracle(case):
         for c, ((L, params, block), orc) in enumerate(zip(chains, orcs)):
             if not live[c]:
                 continue
+            W = slice_potentials(orc)  # the fields this sweep filters with
             if perm:
                 ref = orc.perm_sweep(want_margin=True, block=block)
                 p_gpu, sign = lat.get_perm(c)
@@ -101,8 +142,10 @@ def test_random_combination_matches_oracle(case):
                 ref = orc.sweep(want_margin=True, block=block)
             s, x, a, sw = lat.get_state(c)
             assert sw == k + 1 and a == ref["anchor"], (k, c)
-            err = rel_err(logw[c], ref["logw"]).max()
-            assert err <= tol, (k, c, err)
+            err = rel_err(logw[c], ref["logw"])
+            for sg, p in zip(*np.nonzero(err > tol)):
+                bound = tol + 4 * EPS[prec] * np.log2(orc.N) * orc.M * unit_kappa(orc, W, a, block, sg, p)
+                assert err[sg, p] <= bound, (k, c, sg, p, err[sg, p], bound)
             if perm:
                 firsts, bad = unit_mismatches(x, orc.x, ref["margin"], a, orc.M, orc.perm, tol, block)
             else:
