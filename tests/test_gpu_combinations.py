@@ -3,7 +3,8 @@ C ABI: lattice size (warp and wide kernels), worldline count, number of slices, 
 either sign (Hirsch or Gaussian field), FFBS blocks, permutation updates, the stencil
 convolution, precision, and ragged batches mixing all of these per chain.
 
-Every case runs two sweeps on the GPU and in the oracle from the same seeds.  Per chain:
+Every case runs two sweeps on the GPU and in the oracle from the same seeds, then (if no
+chain has met a CDF edge) one local-update sweep.  Per chain:
 the anchor, the permutation and its sign, the filter log-weights (1e-5 relative in FP32,
 1e-12 in FP64), and the worldlines in draw order, which must agree up to a first
 difference at a draw whose uniform lies within the tolerance of a CDF edge; after a
@@ -158,4 +159,21 @@ def test_random_combination_matches_oracle(case):
                 assert np.allclose(lat.get_sigma(c), orc.sigma, rtol=0, atol=1e-12), (k, c)
             else:
                 assert np.array_equal(s, orc.s), (k, c)
+    if all(live):
+        # then a local-update sweep (Sec. 3.5.1) from the shared state: both sides form the
+        # acceptance ratio in FP64, so a worldline may differ only where one of its
+        # decisions lay within 1e-12 of the ratio
+        lat.local_sweep(1)
+        for c, orc in enumerate(orcs):
+            ref = orc.local_sweep(want_margin=True)
+            s, x, _, sw = lat.get_state(c)
+            assert sw == 3, c
+            bad = [(sg, p) for sg in range(2) for p in range(orc.Nsig)
+                   if not np.array_equal(x[sg, p], orc.x[sg, p]) and not np.any(ref["margin"][sg, p] < 1e-12)]
+            assert not bad, (c, bad[:3])
+            if np.array_equal(x, orc.x):
+                if orc.gauss:
+                    assert np.allclose(lat.get_sigma(c), orc.sigma, rtol=0, atol=1e-12), c
+                else:
+                    assert np.array_equal(s, orc.s), c
     lat.close()
