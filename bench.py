@@ -528,7 +528,7 @@ def main():
                            if not args.block else "FFBS blocks: the f-message working set is B slices per group"},
                 "particle_slice_updates_per_s": value * part_slices,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * (nclasses + 2), "clocks": clocks, "fp64_plain": fp64,
+                "gpu_launches": args.steps * (nclasses + 2 + (1 if args.perm else 0)), "clocks": clocks, "fp64_plain": fp64,
                 "fp32_diagnostics": diag, "local_update": local_upd}
         print(json.dumps(line), flush=True)
     if world > 1:
