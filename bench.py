@@ -436,6 +436,15 @@ def main():
                 "alg_bytes_per_launch": alg_bytes,
                 "alu": {"achieved_tflops": achieved_flops, "peak_tflops": peak_alu,
                         "frac": achieved_flops / peak_alu, "peak_source": alu_src}}
+    # the Gibbs/measure kernel: per site-slice two int32 counts read and cleared (16 B)
+    # and the field bits written twice (2 x 1 bit); the counts were just written by the
+    # FFBS atomics and sit in L2, so HBM is not what bounds it
+    site_slices = sum(M * L * L for (L, M, _) in shapes)
+    gibbs_bytes = site_slices * (16.0 + 0.25)
+    roofline["gibbs"] = {"kernel": "slice_kernel", "kernel_ms": slice_avg, "alg_bytes_per_launch": gibbs_bytes,
+                         "achieved": gibbs_bytes / (slice_avg / 1e3) / 1e9, "unit": "GB/s",
+                         "frac_of_hbm": gibbs_bytes / (slice_avg / 1e3) / 1e9 / hbm_peak,
+                         "note": "latency-bound: L2-resident counts, short CTAs"}
 
     # FP32 diagnostics over the sweeps run so far (degenerate draws are counted, not raised)
     obs = lat.measure(reset=True)
