@@ -83,24 +83,25 @@ def stop_clocks(proc, f, path, device):
 
 def cpu_oracle_sample(target_s=12.0):
     """Time the FP64 oracle (OpenMP over worldlines) on the first k worldlines of each
-    spin of chain 0 for one sweep, k sized for about target_s seconds after an untimed
-    warm-up sweep; extrapolate per worldline to the whole 64-chain batch."""
+    spin of chain 0 for one sweep, k grown until the sweep takes at least half of
+    target_s (after an untimed warm-up sweep); extrapolate per worldline to the whole
+    64-chain batch."""
     import oracle
 
     w = WORK
     args = (w["L"], w["t"], w["U"], w["beta"], w["dtau"], w["filling"], 0)
     cores = oracle.num_threads()
-    k = max(1, cores // 2)  # 2k worldlines: one per thread
-    oracle.Chain(*args).sweep(nwl_limit=k)  # library load, thread pool start
-    orc = oracle.Chain(*args)
-    t0 = time.perf_counter()
-    orc.sweep(nwl_limit=k)
-    dt = time.perf_counter() - t0
-    k2 = max(k, min(orc.Nsig, int(k * target_s / max(dt, 1e-3)) // k * k))
-    orc2 = oracle.Chain(*args)
-    t0 = time.perf_counter()
-    orc2.sweep(nwl_limit=k2)
-    dt2 = time.perf_counter() - t0
+    step = max(1, cores // 2)  # 2 step worldlines: one per thread
+    oracle.Chain(*args).sweep(nwl_limit=step)  # library load, thread pool start
+    k2 = step
+    while True:
+        orc2 = oracle.Chain(*args)
+        t0 = time.perf_counter()
+        orc2.sweep(nwl_limit=k2)
+        dt2 = time.perf_counter() - t0
+        if dt2 >= 0.5 * target_s or k2 >= orc2.Nsig:
+            break
+        k2 = min(orc2.Nsig, max(k2 + step, int(k2 * target_s / max(dt2, 1e-3)) // step * step))
     per_wl = dt2 / (2 * k2)
     total_wl = w["chains"] * 2 * orc2.Nsig
     return {"value": 1.0 / (per_wl * total_wl), "unit": "sweeps/s", "cores": cores, "kind": "oracle",
