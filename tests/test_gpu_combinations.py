@@ -177,3 +177,45 @@ def test_random_combination_matches_oracle(case):
                 else:
                     assert np.array_equal(s, orc.s), c
     lat.close()
+
+
+def test_autotune_keeps_results_with_every_option():
+    """The CTA-shape autotuner times throwaway copies that carry the context's blocks,
+    permutation updates and convolution form, and leaves the chains untouched: a context
+    tuned after one sweep continues bit for bit like one that was never tuned."""
+    from paper_2510_13866_gb300 import Lattice
+
+    Ls = [8, 12, 12, 6]
+    pars = [(1.0, 4.0, 1.0, 0.1, 1.0), (1.0, -4.0, 0.8, 0.1, 0.5), (1.0, 2.0, 1.2, 0.1, 0.25),
+            (1.0, 8.0, 0.5, 0.1, 1.0)]
+    blocks = [3, 0, 5, 2]
+
+    def make():
+        lat = Lattice(Ls, [60, 61, 62, 63], precision="fp32")
+        for c, (p, b) in enumerate(zip(pars, blocks)):
+            lat.set_params(*p, chain=c)
+            if b:
+                lat.set_block(b, chain=c)
+        lat.set_permutations(True)
+        lat.set_conv("stencil")
+        return lat
+
+    ref = make()
+    lw_ref = ref.sweep(3, logw=True)
+    st_ref = [(ref.get_state(c), ref.get_perm(c)) for c in range(len(Ls))]
+    sig_ref = ref.get_sigma(1)
+    ref.close()
+
+    lat = make()
+    lat.sweep(2)
+    lat.autotune(trial_sweeps=2)
+    assert all(lat.get_state(c)[3] == 2 for c in range(len(Ls)))
+    lw = lat.sweep(1, logw=True)
+    for c in range(len(Ls)):
+        assert np.array_equal(lw[c], lw_ref[c]), c
+        (s, x, a, sw), (perm, sign) = lat.get_state(c), lat.get_perm(c)
+        (s0, x0, a0, sw0), (perm0, sign0) = st_ref[c]
+        assert np.array_equal(s, s0) and np.array_equal(x, x0) and a == a0 and sw == sw0 == 3, c
+        assert np.array_equal(perm, perm0) and sign == sign0, c
+    assert np.array_equal(lat.get_sigma(1), sig_ref)
+    lat.close()
