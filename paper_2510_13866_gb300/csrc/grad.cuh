@@ -54,6 +54,11 @@ __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 template <typename T>
 __device__ __forceinline__ void atomic_add_t(T *p, T v) { atomicAdd(p, v); }
 
+// four FP32 reductions into one 16-byte aligned global address (sm_90 and later)
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
 template <typename T, int L>
 __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
     using G = GradGeo<T, L>;
@@ -121,6 +126,8 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
         const uint32_t *scol = srow + (long long)M * L * cd.wpl;
         const T *vlog = vlog_all ? vlog_all + cd.v_off + (long long)sg * M * N : nullptr;
         T *dvp = dv_all ? dv_all + cd.v_off + (long long)sg * M * N : nullptr;
+        // vector reductions need every slice's row start 16-byte aligned
+        const bool dv_v4 = dvp && (N % 4 == 0) && (reinterpret_cast<uintptr_t>(dvp) & 15) == 0;
         const int x00 = st.x[cd.x_off + (long long)wl0 * M];
         const int x01 = has1 ? int(st.x[cd.x_off + (long long)wl1 * M]) : x00;
         const int ax0 = x00 % L, ay0 = x00 / L, ax1 = x01 % L, ay1 = x01 / L;
@@ -345,10 +352,28 @@ __global__ void __launch_bounds__(128) grad_kernel(DevState st, GradLaunch gk) {
                 if (dvp && active) {
                     const T iz0 = T(1) / z0, iz1 = has1 ? T(1) / z1 : T(0);
                     T *dvl = dvp + (long long)l * N;
+                    bool done = false;
+                    if constexpr (sizeof(T) == 4 && L % 4 == 0) {
+                        // even slices: the lane's L sites are contiguous (site r + L gl), so
+                        // they go out as 16-byte vector reductions, one L2 sector each
+                        if (!(l & 1) && dv_v4) {
+                            T *q = dvl + L * gl;
 #pragma unroll
-                    for (int r = 0; r < L; ++r) {
-                        const V m = vmul(f[r], b[r]);
-                        atomic_add_t<T>(dvl + site(l, r), m.x * iz0 + m.y * iz1);
+                            for (int r = 0; r < L; r += 4) {
+                                const V m0 = vmul(f[r], b[r]), m1 = vmul(f[r + 1], b[r + 1]);
+                                const V m2 = vmul(f[r + 2], b[r + 2]), m3 = vmul(f[r + 3], b[r + 3]);
+                                red_add_v4(q + r, m0.x * iz0 + m0.y * iz1, m1.x * iz0 + m1.y * iz1,
+                                           m2.x * iz0 + m2.y * iz1, m3.x * iz0 + m3.y * iz1);
+                            }
+                            done = true;
+                        }
+                    }
+                    if (!done) {
+#pragma unroll
+                        for (int r = 0; r < L; ++r) {
+                            const V m = vmul(f[r], b[r]);
+                            atomic_add_t<T>(dvl + site(l, r), m.x * iz0 + m.y * iz1);
+                        }
                     }
                 }
                 // b_l = W_l . H_l, renormalised
