@@ -64,6 +64,7 @@ def check(lat, params, tol_lz, tol_g, chains, v=None, v_np=None):
     ("fp32", 16, 1.0, 0.05, 1.0, 0),
     ("fp32", 3, 0.6, 0.1, 2 / 9 * 2, 1),
     ("fp32", 12, 0.5, 0.05, 0.875, 4),
+    ("fp32", 32, 0.3, 0.1, 1 / 128, 0),   # four worldlines per spin: 32-lane groups
     ("fp64", 8, 0.8, 0.1, 1.0, 0),
     ("fp64", 6, 0.5, 0.1, 1 / 3, 2),
 ])
