@@ -143,6 +143,32 @@ def test_filter_matches_dense_transfer_product(orc, L, M, dtau, U):
             assert abs(lz - ref) <= 1e-12 * max(1.0, abs(ref))
 
 
+def test_filter_keeps_relative_accuracy_far_from_the_peak(orc):
+    """A potential that pulls the message onto one site (W = e^25 there, 1 elsewhere) leaves
+    a loop anchored four steps away in x and y with a weight about 1e-10 of the peak.  The
+    oracle's direct convolution sums non-negative terms, so its log-weight still matches
+    the dense transfer product (scipy expm, also non-negative sums) to 1e-12 relative: the
+    oracle has no rounding floor relative to the peak, which makes it the reference for the
+    FFT path's floor."""
+    L, dtau = 8, 0.1
+    N = L * L
+    G = dense_G(L, 1.0, dtau)
+    g, _ = orc.g_table(L, 1.0, dtau)
+    sink, xa = 0, 4 + L * 4
+    for M in (4, 6, 8):
+        W = np.ones((M, N))
+        W[:, sink] = math.exp(25.0)
+        v = np.zeros(N)
+        v[xa] = 1.0
+        for i in range(M):
+            v = G @ (W[i] * v)
+        kappa = v.max() / v[xa]
+        assert kappa > 1e9
+        ref = math.log(v[xa])
+        lz = orc.filter_logz(L, M, g, W, 0, xa)
+        assert abs(lz - ref) <= 1e-12 * max(1.0, abs(ref)), (M, kappa, lz, ref)
+
+
 def _enumerate_paths(L, M, g, W, a, xa):
     """All closed paths with x_a held: returns (paths [P][M], weights [P])."""
     N = L * L
