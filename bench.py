@@ -145,12 +145,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-GRAD_WORKLOAD = ("adjoint (config 4): L=16 (N=256) t=1 U=4 beta=4 dtau=0.05 (M=80) half filling, 128 chains; "
+GRAD_WORKLOAD = ("adjoint: L=16 (N=256) t=1 U=4 beta=4 dtau=0.05 (M=80) half filling, 128 chains; "
                  "log Z, d log Z/d v and d log Z/d t per call, BF16 checkpoints every 9 slices")
 
 
 def run_grad(args):
-    """Adjoint evaluations per second (hqmc_log_weight_grad) on the config-4 workload."""
+    """Adjoint evaluations per second (hqmc_log_weight_grad) on the L=16, 128-chain adjoint workload."""
     import numpy as np
     import torch
 
@@ -213,7 +213,7 @@ def run_grad(args):
 
 
 WORKLOADS = {
-    "L32": "config 2 (the headline): " + WORKLOAD,
+    "L32": "the headline: " + WORKLOAD,
     "ragged": ("256 ragged chains, L in {8,12,16,24,32,48}, beta in {2,4,6}, U in {2,4,8}, filling in "
                "{0.5,0.875,1}, dtau=0.05, drawn per chain from Philox key (1,0); one graph replay per sweep"),
     "L64": "2D Hubbard L=64 (N=4096) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",

@@ -1,6 +1,6 @@
-"""Write the oracle regression fixture config1_first_sweeps.json.
+"""Write the oracle regression fixture l4_beta2_first_sweeps.json.
 
-Config 1 of the benchmark family: L=4 (N=16), t=1, U=4, beta=2, dtau=0.1 (M=20), half
+The plain-method case: L=4 (N=16), t=1, U=4, beta=2, dtau=0.1 (M=20), half
 filling (8 up + 8 down worldlines), Philox seed 0.  The values are the oracle's own
 (FP64) after 3 sweeps: the anchor slices, the filter log-weights of each sweep and the
 final worldlines and field.  This script calls only oracle/; the fixture locks the
@@ -35,6 +35,6 @@ def compute():
 
 
 if __name__ == "__main__":
-    with open(os.path.join(HERE, "config1_first_sweeps.json"), "w") as f:
+    with open(os.path.join(HERE, "l4_beta2_first_sweeps.json"), "w") as f:
         json.dump(compute(), f, indent=1)
         f.write("\n")

@@ -1,4 +1,4 @@
-"""The oracle against its stored regression fixture (tests/golden/config1_first_sweeps.json,
+"""The oracle against its stored regression fixture (tests/golden/l4_beta2_first_sweeps.json,
 written by tests/golden/make_golden.py from oracle/ alone), and the FP64 GPU context
 against the same fixture."""
 import json
@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-FIX = json.load(open(os.path.join(HERE, "golden", "config1_first_sweeps.json")))
+FIX = json.load(open(os.path.join(HERE, "golden", "l4_beta2_first_sweeps.json")))
 
 
 def test_oracle_reproduces_fixture(orc):

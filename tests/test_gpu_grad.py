@@ -157,7 +157,7 @@ def test_autograd_function_matches_adjoint():
     lat.close()
 
 
-def test_grad_config4_sampled():
+def test_grad_l16_128_chains_sampled():
     """L=16 (N=256), U=4, beta=4, dtau=0.05 (M=80), half filling, 128 chains, default BF16
     checkpoints every 9 slices; oracle check of one chain, invariants on all."""
     params = (1.0, 4.0, 4.0, 0.05, 1.0)

@@ -108,7 +108,7 @@ def test_ragged_batch_parity(prec):
 
 
 def test_fp64_many_sweeps_track_the_oracle():
-    """Config-1 parameters (L=4, U=4, beta=2, dtau=0.1, half filling, seed 0):
+    """The plain-method case (L=4, U=4, beta=2, dtau=0.1, half filling, seed 0):
     the FP64 GPU chain and the oracle chain stay identical for 200 sweeps."""
     params = (1.0, 4.0, 2.0, 0.1, 1.0)
     lat = make(4, [0], "fp64", *params)
@@ -122,8 +122,8 @@ def test_fp64_many_sweeps_track_the_oracle():
     lat.close()
 
 
-def test_fp32_config1_tracks_until_an_edge():
-    """FP32 at config-1 parameters: sweeps agree until a draw lands on a CDF edge."""
+def test_fp32_l4_tracks_until_an_edge():
+    """FP32 in the plain-method case (L=4, U=4, beta=2): sweeps agree until a draw lands on a CDF edge."""
     params = (1.0, 4.0, 2.0, 0.1, 1.0)
     lat = make(4, [0], "fp32", *params)
     orc = oracle.Chain(4, *params, 0)
@@ -233,7 +233,7 @@ def test_invalid_parameters_are_rejected():
     lat.close()
 
 
-def test_full_size_config2_sampled():
+def test_full_size_l32_64_chains_sampled():
     """L=32, U=4, beta=4, dtau=0.05 (M=80), 512+512 worldlines, 64 chains, in the
     benchmark's launch configuration; the oracle recomputes a sample of worldlines
     (the first 6 of each spin of chains 0 and 37)."""

@@ -54,7 +54,7 @@ def test_wide_first_sweep_parity(L, beta, dtau, fill, nwl):
 
 
 def test_wide_in_a_ragged_batch():
-    """L = 8, 48, 16, 64 chains in one context (config-3-like mix of sizes, fillings, U)."""
+    """L = 8, 48, 16, 64 chains in one context (a ragged mix of sizes, fillings and U)."""
     Ls = [8, 48, 16, 64]
     pars = [(1.0, 4.0, 0.5, 0.05, 0.875), (1.0, 8.0, 0.3, 0.05, 0.875), (1.0, 2.0, 0.4, 0.05, 0.5),
             (1.0, 4.0, 0.2, 0.05, 1.0)]
