@@ -104,21 +104,22 @@ def free_two_worldlines(L, t, beta):
     return p_swap, e_sgn, dlogzf
 
 
-@pytest.mark.parametrize("with_local", [False, True])
-def test_free_worldlines_sample_the_fermionic_closed_forms(with_local):
-    """U = 0, L = 3, two worldlines per spin, t = 1, beta = 0.5, dtau = 0.25 (M = 2), where
-    P(swap) = 0.22 and E[sgn] = 0.57 per spin.
-    Independent chains (30 sweeps each, optionally each followed by a local sweep) give
-    P(swap) and E[sgn] per spin within 4 standard errors of Tr(T^2)/(Tr(T)^2 + Tr(T^2))
-    and its companion; without local sweeps, the sign-reweighted link estimator of one
-    spin, E[sgn sum links] / E[sgn], lies within 4 standard errors of d log Z_F / dt."""
-    L, t, beta, dtau = 3, 1.0, 0.5, 0.25
+@pytest.mark.parametrize("with_local,block,dtau", [(False, 0, 0.25), (True, 0, 0.25), (False, 2, 0.125)])
+def test_free_worldlines_sample_the_fermionic_closed_forms(with_local, block, dtau):
+    """U = 0, L = 3, two worldlines per spin, t = 1, beta = 0.5, where P(swap) = 0.22 and
+    E[sgn] = 0.57 per spin (the closed forms hold at any dtau, since G^M = exp(beta t A)).
+    Independent chains (30 sweeps each: closed-loop FFBS at M = 2, optionally each sweep
+    followed by a local sweep, or FFBS in blocks of 2 slices at M = 4) give P(swap) and
+    E[sgn] per spin within 4 standard errors of Tr(T^2)/(Tr(T)^2 + Tr(T^2)) and its
+    companion; without local sweeps, the sign-reweighted link estimator of one spin,
+    E[sgn sum links] / E[sgn], lies within 4 standard errors of d log Z_F / dt."""
+    L, t, beta = 3, 1.0, 0.5
     p_swap, e_sgn, dlogzf = free_two_worldlines(L, t, beta)
     swapped, sg_links, sgns = [], [], []
     for seed in range(800):
         ch = oracle.Chain(L, t, 0.0, beta, dtau, 4.0 / 9.0, 1000 + seed)
         for _ in range(30):
-            out = ch.perm_sweep()
+            out = ch.perm_sweep(block=block)
             if with_local:
                 ch.local_sweep()
         for sg in range(2):
