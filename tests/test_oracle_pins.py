@@ -459,6 +459,29 @@ def test_sweep_two_particle_exact_attractive(orc):
     assert abs(em - E_ex) < 4.5 * ee + 1e-4, (em, ee, E_ex)
 
 
+@pytest.mark.parametrize("block,with_local", [(2, False), (0, True), (3, True)])
+def test_sweep_two_particle_exact_attractive_blocks_and_local(orc, block, with_local):
+    """U < 0 (Gaussian field) with FFBS in blocks and/or every FFBS sweep followed by a
+    local-update sweep: the composition still samples the exact two-particle measure
+    (D and E_kin against the transfer matrix with the field integrated out)."""
+    L, U, dtau, beta = 3, -4.0, 0.25, 1.0
+    M = 4
+    D_ex, E_ex = two_particle_exact(L, 1.0, U, dtau, M)
+    ch = orc.Chain(L=L, t=1.0, U=U, beta=beta, dtau=dtau, filling=2.0 / (L * L), seed=20 + block)
+    Ds, Es = [], []
+    for k in range(24000):
+        out = ch.local_sweep() if with_local and k % 2 else ch.sweep(block=block)
+        if k < 500:
+            continue
+        m = orc.measure(L, M, out["hist"], want_fields=False)
+        Ds.append(m["d"] / (M * L * L))
+        Es.append(-(1.0 / beta) * out["links"].sum() / (L * L))
+    dm, de = _batch_stats(Ds)
+    em, ee = _batch_stats(Es)
+    assert abs(dm - D_ex) < 4.5 * de + 1e-4, (dm, de, D_ex)
+    assert abs(em - E_ex) < 4.5 * ee + 1e-4, (em, ee, E_ex)
+
+
 def test_box_muller_normal(orc):
     """Box-Muller output of independent uniforms is standard normal (Kolmogorov-Smirnov)."""
     from scipy import stats
