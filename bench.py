@@ -122,7 +122,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     orc.sweep(nwl_limit=1)
     one = time.perf_counter() - t0
-    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)  # whole run within a few minutes
     k = max(1, min(orc.Nsig, int(budget / max(one, 1e-3) / 2)))
     for _ in range(args.warmup):
         orc.sweep(nwl_limit=k)
@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="CPU seconds the reference arm (the oracle) spreads over its warm-up and timed steps")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS) + ["grad16"],
