@@ -157,6 +157,13 @@ class Lattice:
             self._ctx = C.c_void_p()
         self._ws = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __del__(self):
         try:
             self.close()
