@@ -50,7 +50,8 @@ typedef struct hqmc_ctx hqmc_ctx;
 #define HQMC_ERR_ARG (-1)         /* invalid argument (see each call) */
 #define HQMC_ERR_NOMEM (-2)       /* device allocation failed or workspace too small */
 #define HQMC_ERR_CUDA (-3)        /* a CUDA runtime call failed */
-#define HQMC_ERR_TIMEOUT (-4)     /* a bounded device-side wait expired */
+#define HQMC_ERR_TIMEOUT (-4)     /* reserved: no kernel of this library waits on a flag, a peer or a
+                                   * barrier it does not own, so no call returns it today */
 #define HQMC_ERR_STATE (-5)       /* call out of order (e.g. sweep before set_params) */
 #define HQMC_ERR_UNSUPPORTED (-6) /* lattice size or mode not built into this library */
 #define HQMC_ERR_NUMERIC (-7)     /* a draw met an all-zero CDF or log Z met a non-positive amplitude */
@@ -180,7 +181,7 @@ int hqmc_attach_workspace(hqmc_ctx *ctx, void *dev_ptr, size_t bytes);
  * anchor-slice position held of prod_l W_l(x_l) G(x_{l+1} - x_l), evaluated with the
  * field before that sweep's Gibbs step.  The call blocks until the sweeps finish.
  * Numerical degeneracies are counted (hqmc_obs.n_degenerate, n_nonpositive), not raised.
- * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA, HQMC_ERR_TIMEOUT. */
+ * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA. */
 int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
 
 /* Run n_sweeps >= 0 local-update sweeps (Sec. 3.5.1, Eq. Rlocal, read in the position
@@ -313,9 +314,13 @@ int hqmc_profile_read(hqmc_ctx *ctx, double *ffbs_ms, double *slice_ms, int *n_s
  * every device that loads the library keeps until the process exits.
  *
  *   L, M, Nsig      lattice size (a built size, L <= 32), slices, worldlines per spin
- *   t, U, dtau      model parameters as in hqmc_set_params
- *   seed, sweep     Philox key and sweep index: the call draws exactly what sweep
- *                   number `sweep` of a context chain with this seed draws in its FFBS
+ *   t, U, dtau      model parameters as in hqmc_set_params, but U >= 0 only (the discrete
+ *                   Hirsch field; U < 0 is HQMC_ERR_ARG)
+ *   seed, sweep     Philox key and sweep index: the call draws what sweep number `sweep`
+ *                   of a context chain with this seed draws in its FFBS, provided that
+ *                   chain runs the context defaults -- the closed loop (no hqmc_set_block),
+ *                   HQMC_CONV_FFT and no permutation ever used; a chain with blocks, the
+ *                   stencil or permutations draws differently
  *   s               device, [M][N] int8 field (+1/-1), read only
  *   x               device, [2][Nsig][M] int32 sites, read and overwritten with the new paths
  *   logw            device, [2][Nsig] double, receives the filter log-weights
@@ -326,13 +331,15 @@ int hqmc_profile_read(hqmc_ctx *ctx, double *ffbs_ms, double *slice_ms, int *n_s
  * field, 16-bit worldlines, a [2][M][N] int32 histogram; about 6 B per site-slice plus
  * 4 B per worldline-slice) plus at least one slot of M*N*8 bytes (16 for FP64); a problem
  * that does not fit 32 MiB is rejected with HQMC_ERR_SCRATCH.  Fewer slots than pairs
- * only lowers parallelism.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current, so make that first call
- * before any stream capture.  All calls share the one array and each call re-initialises
- * what must start at zero; calls that overlap on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.
- * Errors: HQMC_ERR_ARG (null pointers, sizes, or s/x values out of range),
- * HQMC_ERR_UNSUPPORTED, HQMC_ERR_SCRATCH, HQMC_ERR_CUDA, HQMC_ERR_NUMERIC. */
+ * only lowers parallelism.  Every call looks up the array's device address in the current
+ * device's context (cudaGetSymbolAddress).  All calls share the one array and each call
+ * re-initialises what must start at zero; calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Errors: HQMC_ERR_ARG (null pointers, sizes, U < 0, or s/x values out of range; x and
+ * logw are then untouched), HQMC_ERR_UNSUPPORTED, HQMC_ERR_SCRATCH, HQMC_ERR_CUDA,
+ * HQMC_ERR_NUMERIC.  HQMC_ERR_NUMERIC (a draw met an all-zero CDF, where the worldline
+ * kept its site, or a log-weight met a non-positive amplitude) is reported after the
+ * sweep: x and logw then already hold that sweep's outputs. */
 int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, double dtau, uint64_t seed,
                       uint64_t sweep, const int8_t *s, int32_t *x, double *logw, int precision,
                       void *stream);

@@ -23,17 +23,29 @@ static cudaError_t ffbs_go(const DevState &st, const FfbsLaunch &fl, int grid, i
     return cudaGetLastError();
 }
 
-// sets the kernel's dynamic shared-memory limit and reports resident CTAs per SM
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`, never lowers it: the
+// limit belongs to the whole process, and another context (or the no-allocation entry
+// point) may launch the same kernel with a wider CTA.
+template <typename K>
+static cudaError_t raise_smem_limit(K kernel, size_t bytes) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (size_t(fa.maxDynamicSharedSizeBytes) >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
+// raises the kernel's dynamic shared-memory limit as needed and reports resident CTAs per SM
 template <typename T, int L>
 static cudaError_t ffbs_occ(int wpc, int *blocks) {
     const size_t sm = ffbs_smem_bytes_t<T, L>(wpc);
     cudaError_t e = cudaSuccess;
     for (auto kx : {ffbs_kernel<T, L, true, false>, ffbs_kernel<T, L, true, true>, ffbs_kernel<T, L, false, true>}) {
-        e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        e = raise_smem_limit(kx, sm);
         if (e != cudaSuccess) return e;
     }
     auto k = ffbs_kernel<T, L, false, false>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    e = raise_smem_limit(k, sm);
     if (e != cudaSuccess) return e;
     // both instantiations are held to the same launch bounds; the closed-loop one sizes the grid
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, wpc * 32, sm);

@@ -19,7 +19,7 @@ template <typename T, int L>
 static cudaError_t grad_occ(int *blocks) {
     const size_t sm = grad_smem_bytes_t<T, L>(kGradWarps);
     auto k = grad_kernel<T, L>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    cudaError_t e = raise_smem_limit(k, sm);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kGradWarps * 32, sm);
 }

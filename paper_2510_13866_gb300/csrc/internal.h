@@ -102,7 +102,9 @@ __host__ __device__ inline int ffbs_nblk(int block, int M) {
     return (M + B - 1) / B;
 }
 
-enum : unsigned { kStatusDegenerate = 1u, kStatusNonPositive = 2u, kStatusTimeout = 4u };
+// device status bits (no kernel of this library waits on a flag, a peer or a barrier it does
+// not own, so there is no timeout bit)
+enum : unsigned { kStatusDegenerate = 1u, kStatusNonPositive = 2u };
 
 // One launch of the FFBS kernel covers the chains of one lattice size.  Its work units are
 // (worldline pair, block) with the blocks of one pair independent given their held ends.

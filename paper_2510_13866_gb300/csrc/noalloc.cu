@@ -3,8 +3,8 @@
 // occupancy histogram and the per-group f_l slots) lives in one file-scope
 // __device__ array of fixed size.  The FFBS kernel itself is the library's usual one.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/hqmc.h"
 #include "internal.h"
@@ -27,10 +27,6 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr unsigned kStatusBadInput = 8u;
-constexpr int kMaxDevices = 256;
-
-std::mutex g_mu;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -151,21 +147,17 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     const size_t slot = size_t(M) * L * L * (f64 ? 16 : 8);
     if (lay.fixed + slot > kStaticScratchBytes) return HQMC_ERR_SCRATCH;
 
-    // the static array's device address, looked up once per device with it current
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HQMC_ERR_CUDA;
+    // the static array's device address in the current device's context, looked up on
+    // every call (the host-side name of the array is not a device address, and a cached
+    // address would go stale after a device reset reloads the module)
     unsigned char *base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
-                return HQMC_ERR_CUDA;
-            }
-            g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HQMC_ERR_CUDA;
         }
-        base = g_scratch_addr[dev];
+        base = static_cast<unsigned char *>(p);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
@@ -199,9 +191,16 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     const long long grid_cap = max_groups / gpc;
     if (grid > grid_cap) grid = grid_cap;
     if (grid < 1) return HQMC_ERR_SCRATCH;
-    int bps = 0;
+    // resident CTAs per SM (this also raises the kernel's shared-memory limit to the
+    // launch's needs): the grid need not exceed one resident wave, since groups take
+    // pairs from a work counter
+    int bps = 0, nsm = 0, dev = 0;
     cudaError_t e = f64 ? ffbs_occupancy_f64(L, wpc, &bps) : ffbs_occupancy_f32(L, wpc, &bps);
     if (e != cudaSuccess) return HQMC_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HQMC_ERR_CUDA;
+    const long long wave = (long long)std::max(1, bps) * std::max(1, nsm);
+    if (grid > wave) grid = wave;
 
     static_setup_kernel<<<1, 256, 0, st>>>(base, lay, cd, tab, (unsigned long long)sweep);
     if (cudaGetLastError() != cudaSuccess) return HQMC_ERR_CUDA;
@@ -245,7 +244,6 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     if (cudaMemcpyAsync(&acc, base + lay.meas, sizeof(MeasAcc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return HQMC_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HQMC_ERR_CUDA;
-    if (status & kStatusTimeout) return HQMC_ERR_TIMEOUT;
     if (status || acc.degenerate || acc.nonpositive) return HQMC_ERR_NUMERIC;
     return HQMC_OK;
 }

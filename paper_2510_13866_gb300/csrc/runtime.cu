@@ -686,7 +686,6 @@ int check_status(hqmc_ctx *c) {
     HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
     if (stt) {
         HQMC_CUDA(c, cudaMemsetAsync(c->st.status, 0, sizeof(unsigned), c->stream));
-        if (stt & kStatusTimeout) return fail(c, HQMC_ERR_TIMEOUT, "device wait expired");
         return fail(c, HQMC_ERR_NUMERIC,
                     (stt & kStatusDegenerate) ? "a draw met an all-zero CDF" : "log Z met a non-positive amplitude");
     }

@@ -144,6 +144,9 @@ class Lattice:
         self._check(lib().hqmc_set_stream(self._ctx, C.c_void_p(stream.cuda_stream)))
         self.shapes = None
         self.params = None
+        # (t, U, beta, dtau, filling) of every chain as last set, so that a change of t
+        # alone (log_weight) keeps each chain's own U, beta, dtau and filling
+        self.chain_params = [None] * self.n_chains
 
     # -- helpers -----------------------------------------------------------
     def _check(self, rc, ctx=True):
@@ -173,8 +176,13 @@ class Lattice:
     # -- configuration -----------------------------------------------------
     def set_params(self, t, U, beta, dtau, filling, chain=-1):
         self._check(lib().hqmc_set_params(self._ctx, chain, t, U, beta, dtau, filling))
+        p = (float(t), float(U), float(beta), float(dtau), float(filling))
         if chain == -1:
-            self.params = (float(t), float(U), float(beta), float(dtau), float(filling))
+            self.params = p
+            self.chain_params = [p] * self.n_chains
+        else:
+            self.chain_params[int(chain)] = p
+            self.params = p if all(q == p for q in self.chain_params) else None
         self.shapes = None
 
     def set_block(self, B, chain=-1):
@@ -411,10 +419,12 @@ def _log_weight_function():
         @staticmethod
         def forward(ctx, lat, v, t):
             tv = float(t)
-            if lat.params is None:
-                raise ValueError("set_params first")
-            if tv != lat.params[0]:
-                lat.set_params(tv, *lat.params[1:])
+            if any(p is None for p in lat.chain_params):
+                raise ValueError("set_params first (for every chain)")
+            # only t changes: every chain keeps its own U, beta, dtau and filling
+            for c, p in enumerate(list(lat.chain_params)):
+                if p[0] != tv:
+                    lat.set_params(tv, *p[1:], chain=c)
             lz, dv, dt = lat.log_weight_grad(v=v.detach(), want_dv=True)
             sizes = [2 * M * L * L for L, M, _ in lat.shapes]
             ctx.save_for_backward(dv)

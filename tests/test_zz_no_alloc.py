@@ -81,3 +81,41 @@ def test_noalloc_rejects_what_does_not_fit_and_bad_input():
     lw_dev = torch.zeros(2 * Ns, dtype=torch.float64, device="cuda")
     ptrs = [C.c_void_p(a.data_ptr()) for a in (s_dev, x_dev, lw_dev)]
     assert lib.hqmc_ffbs_noalloc(L, M, Ns, 1.0, 4.0, 0.1, 0, 0, *ptrs, 0, stream) == -1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_noalloc_leaves_a_wide_context_launchable(prec):
+    """A context whose CTAs carry 8 worldline groups needs the FFBS kernel's shared-memory
+    limit of that shape; a no-allocation call in between (4 warps per CTA) must not lower
+    it, so the context's next sweep still runs and matches a context that never saw it."""
+    import torch
+
+    from paper_2510_13866_gb300 import Lattice, hqmc
+
+    L, t, U, beta, dtau, seed = 32, 1.0, 4.0, 0.4, 0.05, 5
+    ref = Lattice(L, [seed], precision=prec)
+    ref.set_params(t, U, beta, dtau, 0.25)
+    ref.set_class_launch(L, 8)
+    ref.sweep(1)
+    lw_ref = ref.sweep(1, logw=True)[0]
+    ref.close()
+
+    lat = Lattice(L, [seed], precision=prec)
+    lat.set_params(t, U, beta, dtau, 0.25)
+    lat.set_class_launch(L, 8)
+    lat.sweep(1)
+    s, x, _, _ = lat.get_state(0)
+    _, M, Ns = lat.shapes[0]
+    lib = hqmc.lib()
+    stream = torch.cuda.current_stream()
+    s_dev = torch.from_numpy(s.copy()).cuda()
+    x_dev = torch.from_numpy(x.copy()).cuda()
+    lw_dev = torch.zeros(2 * Ns, dtype=torch.float64, device="cuda")
+    p = hqmc.HQMC_FP64 if prec == "fp64" else hqmc.HQMC_FP32
+    rc = lib.hqmc_ffbs_noalloc(L, M, Ns, t, U, dtau, seed, 1, C.c_void_p(s_dev.data_ptr()),
+                               C.c_void_p(x_dev.data_ptr()), C.c_void_p(lw_dev.data_ptr()), p,
+                               C.c_void_p(stream.cuda_stream))
+    assert rc == 0, hqmc.ERRORS.get(rc, rc)
+    lw = lat.sweep(1, logw=True)[0]  # raised HQMC_ERR_CUDA when the limit had been lowered
+    lat.close()
+    assert np.array_equal(lw, lw_ref)
