@@ -105,8 +105,11 @@ def cpu_oracle_sample(target_s=12.0):
     per_wl = dt2 / (2 * k2)
     total_wl = w["chains"] * 2 * orc2.Nsig
     return {"value": 1.0 / (per_wl * total_wl), "unit": "sweeps/s", "cores": cores, "kind": "oracle",
-            "sample": f"chain 0, first {k2} worldlines of each spin, 1 sweep ({dt2:.1f} s), "
-                      f"extrapolated per worldline to {total_wl} worldlines"}
+            "rate_kind": "per-worldline rate extrapolated from a sample (not a measured whole sweep)",
+            "worldline_sweeps_per_s": 1.0 / per_wl,
+            "sample": f"chain 0, first {k2} worldlines of each spin, 1 sweep ({dt2:.1f} s): "
+                      f"{1.0 / per_wl:.3g} worldline-sweeps/s, divided by the {total_wl} worldlines of a "
+                      f"whole {w['chains']}-chain sweep"}
 
 
 def run_reference(args):
@@ -134,13 +137,20 @@ def run_reference(args):
     per_wl = sum(times) / (len(times) * 2 * k)
     total_wl = w["chains"] * 2 * orc.Nsig
     value = 1.0 / (per_wl * total_wl)
+    # a step is one sweep of the sample (2k worldlines of chain 0), which is what ms_per_step
+    # measures; value is the per-worldline rate of those steps divided over the 65536
+    # worldlines of a whole 64-chain sweep (the oracle cannot run a whole sweep in minutes)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_worldlines_per_spin": k},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "rate_kind": "per-worldline rate extrapolated from a sample: ms_per_step is one sweep of the sample, "
+                         "value = 1 / (seconds per worldline-sweep x worldlines of a whole sweep)",
+            "config": {"workload": WORKLOAD, "sample_worldlines_per_spin": k, "sample_chains": 1,
+                       "worldlines_per_whole_sweep": total_wl},
             "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": cores, "kind": "oracle",
+                             "worldline_sweeps_per_s": 1.0 / per_wl,
                              "sample": f"each step: chain 0, first {k} worldlines of each spin, one sweep; "
-                                       f"extrapolated to {total_wl} worldlines"},
+                                       f"per-worldline rate divided over {total_wl} worldlines"},
             "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -218,13 +228,13 @@ WORKLOADS = {
                "{0.5,0.875,1}, dtau=0.05, drawn per chain from Philox key (1,0); one graph replay per sweep"),
     "L64": "2D Hubbard L=64 (N=4096) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
     "L128": "2D Hubbard L=128 (N=16384) t=1 U=4 beta=8 dtau=0.05 (M=160) half filling, 16 chains",
-    "paper8": "the paper's timing regime: L=8, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
-    "paper16": "the paper's timing regime: L=16, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
-    "paper32": "the paper's timing regime: L=32, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
+    "paper8": "the paper's regime: L=8, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
+    "paper16": "the paper's regime: L=16, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
+    "paper32": "the paper's regime: L=32, t=1, U=4, beta=32, dtau=1/32 (M=1024), half filling, 1 chain",
 }
 
 
-def workload(name, rank, chains, beta=None):
+def workload(name, rank, chains, beta=None, U=None):
     """(L per chain, params per chain, seeds) of a named workload on rank `rank`."""
     from paper_2510_13866_gb300.shard import chain_seeds
     from paper_2510_13866_gb300.workloads import ragged
@@ -240,7 +250,7 @@ def workload(name, rank, chains, beta=None):
     if name.startswith("paper"):
         L = int(name[5:])
         n = chains or 1
-        return [L] * n, [(1.0, 4.0, 32.0, 1.0 / 32.0, 1.0)] * n, chain_seeds(rank, n)
+        return [L] * n, [(1.0, 4.0 if U is None else U, 32.0, 1.0 / 32.0, 1.0)] * n, chain_seeds(rank, n)
     L = int(name[1:])
     n = chains or 16
     return [L] * n, [(1.0, 4.0, beta if beta else 8.0, 0.05, 1.0)] * n, chain_seeds(rank, n)
@@ -261,30 +271,77 @@ def alu_peak(device):
                     f"{scalar:.1f}; nominal 152 SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz = {nominal:.1f})")
 
 
-def same_accuracy(make, lat64, sweeps):
-    """The FP32 filter against the plain FP64 form at equal work: FP32 chains with the
-    FP64 chains' seeds run the same number of sweeps from the same start.  Both chains of
-    a seed then share their paths until a uniform falls within FP32 rounding of a CDF
-    edge, so each observable's FP32 - FP64 difference is set against the FP64 estimate's
-    statistical error over the independent chains (equal accuracy: |diff| well below it)."""
+def equilibrium_accuracy(obs32, obs64, burn, meas):
+    """The FP32 filter against the plain FP64 form at equilibrium: independent chains of each
+    precision (disjoint seeds) after `burn` sweeps, observables averaged over `meas` further
+    sweeps per chain.  Per observable: both means with their statistical errors over the
+    chains and z = (FP32 - FP64) / sqrt(se32^2 + se64^2); equal accuracy means |z| of order
+    1 and standard errors of the same size."""
     import numpy as np
 
-    lat32 = make("fp32")
-    lat32.sweep(sweeps)
-    obs32, obs64 = lat32.measure(), lat64.measure()
-    same = sum(np.array_equal(lat32.get_state(c)[1], lat64.get_state(c)[1]) for c in range(len(obs64)))
-    lat32.close()
-    names = ("double_occ", "m2", "ekin", "s_pipi")
+    names = ("double_occ", "m2", "ekin", "s_pipi", "density")
     a = np.array([[o[k] for k in names] for o in obs32])
     b = np.array([[o[k] for k in names] for o in obs64])
-    n = len(b)
-    se = b.std(axis=0, ddof=1) / np.sqrt(n) if n > 1 else np.full(len(names), np.nan)
-    out = {"sweeps": sweeps, "chains": n, "chains_with_identical_paths": int(same), "observables": {}}
+    sa = a.std(axis=0, ddof=1) / np.sqrt(len(a))
+    sb = b.std(axis=0, ddof=1) / np.sqrt(len(b))
+    out = {"burn_in_sweeps": burn, "measured_sweeps": meas, "chains_fp32": len(a), "chains_fp64": len(b),
+           "seeds": "FP32 0..63, FP64 10000..10063 (disjoint)", "observables": {}}
     for j, k in enumerate(names):
+        se = float(np.hypot(sa[j], sb[j]))
         d = float(a[:, j].mean() - b[:, j].mean())
-        out["observables"][k] = {"fp32": float(a[:, j].mean()), "fp64": float(b[:, j].mean()),
-                                 "fp64_stat_err": float(se[j]), "diff": d,
-                                 "diff_over_stat_err": d / float(se[j]) if se[j] > 0 else None}
+        out["observables"][k] = {"fp32": float(a[:, j].mean()), "fp32_stat_err": float(sa[j]),
+                                 "fp64": float(b[:, j].mean()), "fp64_stat_err": float(sb[j]),
+                                 "z": d / se if se > 0 else None}
+    zs = [v["z"] for v in out["observables"].values() if v["z"] is not None]
+    out["max_abs_z"] = max(abs(z) for z in zs) if zs else None
+    return out
+
+
+def observables(lat, shapes, sweeps, open_path=True):
+    """Observables of Sec. 4 after the timed region: the chains run `sweeps` more sweeps
+    (with the open-path estimator on for n_k) and every estimate is the sign-reweighted
+    mean over the chains, <O> = sum_c <sO>_c / sum_c <s>_c, with its standard error by the
+    delta method over the independent chains.  S(k) and n_k are given along
+    (0,0) -> (pi,0) -> (pi,pi) -> (0,0), C(r) along (r, 0) and the diagonal (r, r)."""
+    import numpy as np
+
+    L = shapes[0][0]
+    if open_path:
+        lat.set_measure_open(True)  # restarts the accumulators
+    else:
+        lat.measure(reset=True)
+    lat.sweep(sweeps)
+    obs = lat.measure()
+    opn = lat.measure_open() if open_path else None
+    sg = np.array([o["mean_sign"] for o in obs])
+    n = len(sg)
+
+    def est(vals):
+        vals = np.asarray(vals, dtype=float)  # per chain (sign-reweighted within the chain)
+        num = vals * sg.reshape((-1,) + (1,) * (vals.ndim - 1))
+        R = num.mean(axis=0) / sg.mean()
+        resid = num - R[None] * sg.reshape((-1,) + (1,) * (vals.ndim - 1))
+        se = resid.std(axis=0, ddof=1) / np.sqrt(n) / abs(sg.mean()) if n > 1 else np.full(np.shape(R), np.nan)
+        return R, se
+
+    path = [(k, 0) for k in range(L // 2)] + [(L // 2, k) for k in range(L // 2)] + \
+        [(k, k) for k in range(L // 2, -1, -1)]
+    idx = [kx + L * ky for kx, ky in path]
+    out = {"sweeps": sweeps, "chains": n,
+           "mean_sign": {"value": float(sg.mean()), "stat_err": float(sg.std(ddof=1) / np.sqrt(n)) if n > 1 else None},
+           "path": [[2 * kx / L, 2 * ky / L] for kx, ky in path], "path_unit": "pi"}
+    for name in ("double_occ", "m2", "ekin", "s_pipi"):
+        R, se = est([o[name] for o in obs])
+        out[name] = {"value": float(R), "stat_err": float(se)}
+    R, se = est([o["Sk"] for o in obs])
+    out["Sk_path"] = {"value": R[idx].tolist(), "stat_err": se[idx].tolist()}
+    R, se = est([o["Cr"] for o in obs])
+    out["Cr_axis"] = {"value": R[:L // 2 + 1].tolist(), "stat_err": se[:L // 2 + 1].tolist()}
+    dg = [r + L * r for r in range(L // 2 + 1)]
+    out["Cr_diagonal"] = {"value": R[dg].tolist(), "stat_err": se[dg].tolist()}
+    if opn is not None:
+        R, se = est([nk for nk, _ in opn])
+        out["nk_path"] = {"value": R[idx].tolist(), "stat_err": se[idx].tolist()}
     return out
 
 
@@ -294,7 +351,7 @@ def kernel_source_digest(workload="L32"):
     import hashlib
 
     h = hashlib.sha256()
-    files = ("ffbs.cuh", "device_common.cuh") if workload == "L32" else ("ffbs.cuh", "ffbs_big.cuh",
+    files = ("ffbs.cuh", "device_common.cuh") if workload == "L32" else ("ffbs.cuh", "ffbs_wide.cuh",
                                                                           "device_common.cuh")
     for f in files:
         with open(os.path.join(ROOT, "paper_2510_13866_gb300", "csrc", f), "rb") as fh:
@@ -310,7 +367,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=150.0,
                     help="CPU seconds the reference arm (the oracle) spreads over its warm-up and timed steps")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=10,
+                    help="timed sweeps of the plain FP64 form (taken at equilibrium, inside the accuracy run)")
+    ap.add_argument("--acc-burn", type=int, default=100,
+                    help="burn-in sweeps of the FP32 / FP64 equilibrium accuracy comparison (0: skip it)")
+    ap.add_argument("--acc-sweeps", type=int, default=100,
+                    help="measured sweeps per chain of the equilibrium accuracy comparison")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="L32", choices=sorted(WORKLOADS) + ["grad16"],
                     help="L32 (default, the headline configuration), ragged, L64, L128, paper8/16/32 "
@@ -326,6 +388,11 @@ def main():
     ap.add_argument("--beta", type=float, default=None,
                     help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures), "
                          "or of L32 in place of its beta = 4")
+    ap.add_argument("--U", type=float, default=None,
+                    help="U of the paper8/16/32 workloads (default 4; the paper's runs use 1 and 20)")
+    ap.add_argument("--observables", type=int, default=0,
+                    help="after the timed region, run this many measured sweeps and report the Sec. 4 "
+                         "observables (mean sign, D, m2, E_kin, S(k), C(r), n_k) with errors over the chains")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per GPU (default: the workload's own; smaller only for profiling captures)")
     args = ap.parse_args()
@@ -360,11 +427,11 @@ def main():
 
     from paper_2510_13866_gb300 import Lattice
 
-    Ls, pars, seeds = workload(args.workload, rank, args.chains, args.beta)
+    Ls, pars, seeds = workload(args.workload, rank, args.chains, args.beta, args.U)
     nchains = len(Ls)
 
-    def make(precision):
-        lt = Lattice(Ls, seeds, precision=precision, device=local)
+    def make(precision, seed_offset=0):
+        lt = Lattice(Ls, [s + seed_offset for s in seeds], precision=precision, device=local)
         if len(set(pars)) == 1:
             lt.set_params(*pars[0])
         else:
@@ -466,6 +533,9 @@ def main():
     e2e_val = max_over_ranks(te)
     e2e = {"value": world * ke / e2e_val, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": int(8 * sum(2 * ns for (_, _, ns) in shapes)) + 4}
+    phys = None
+    if args.observables > 0 and nclasses == 1:
+        phys = observables(lat, shapes, args.observables)
     # local link updates (Eq. Rlocal in the position basis) on the same chains: one
     # launch per slice colour, then the same Gibbs/measure step; plain launches
     local_upd = None
@@ -485,11 +555,14 @@ def main():
                      "accepted_per_proposal": nacc / proposals, "launches_per_sweep": 5}
     lat.close()
 
-    # plain FP64 form: same kernels in double, one launch per phase, no graph
+    # plain FP64 form: same kernels in double, one launch per phase, no graph; timed at
+    # equilibrium inside the accuracy comparison (disjoint seeds from the FP32 chains)
     fp64 = None
     if args.fp64_steps > 0 and max(Ls) <= 32:
-        lat64 = make("fp64")
-        lat64.sweep(1)
+        lat64 = make("fp64", seed_offset=10_000)
+        burn = max(1, args.acc_burn)
+        lat64.sweep(burn)
+        lat64.measure(reset=True)
         torch.cuda.synchronize()
         e0.record(stream)
         lat64.sweep(args.fp64_steps)
@@ -497,7 +570,8 @@ def main():
         torch.cuda.synchronize()
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         v64 = world * args.fp64_steps / (ms64 / 1e3)
-        fp64 = {"value": v64, "unit": "sweeps/s", "steps": args.fp64_steps, "fp32_over_fp64": value / v64}
+        fp64 = {"value": v64, "unit": "sweeps/s", "steps": args.fp64_steps, "fp32_over_fp64": value / v64,
+                "timed_after_sweeps": burn}
         # the FP64 form's own ALU roofline: the same algorithmic flops per sweep against
         # the measured DFMA rate (it runs the same FFTs in double)
         try:
@@ -509,10 +583,19 @@ def main():
                            "peak_source": "measured in this run: DFMA loop on every SM"}
         except Exception as e:  # noqa: BLE001 -- the rate stands without its roofline
             fp64["alu"] = {"error": str(e)}
-        try:
-            fp64["accuracy"] = same_accuracy(make, lat64, 1 + args.fp64_steps)
-        except Exception as e:  # noqa: BLE001 -- an optional comparison; the line still prints
-            fp64["accuracy"] = {"error": str(e)}
+        if args.acc_burn > 0:
+            try:
+                lat64.sweep(max(0, args.acc_sweeps - args.fp64_steps))
+                obs64 = lat64.measure()
+                lat32 = make("fp32")
+                lat32.sweep(burn)
+                lat32.measure(reset=True)
+                lat32.sweep(max(args.acc_sweeps, args.fp64_steps))
+                obs32 = lat32.measure()
+                lat32.close()
+                fp64["accuracy"] = equilibrium_accuracy(obs32, obs64, burn, max(args.acc_sweeps, args.fp64_steps))
+            except Exception as e:  # noqa: BLE001 -- an optional comparison; the line still prints
+                fp64["accuracy"] = {"error": str(e)}
         lat64.close()
 
     cpu = None
@@ -528,6 +611,8 @@ def main():
             wl = wl.replace("x 64 chains", f"x {nchains} chains")
         if args.workload.startswith("paper") and nchains != 1:
             wl = wl.replace("1 chain", f"{nchains} chains")
+        if args.workload.startswith("paper") and args.U is not None:
+            wl = wl.replace("U=4", f"U={args.U:g}")
         if args.block:
             wl += f"; block FFBS, B={args.block}"
         if args.perm:
@@ -548,6 +633,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (nclasses + 2 + (1 if args.perm else 0)), "clocks": clocks, "fp64_plain": fp64,
                 "fp32_diagnostics": diag, "local_update": local_upd}
+        if phys is not None:
+            line["observables"] = phys
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

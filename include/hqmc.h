@@ -80,13 +80,18 @@ typedef struct {
      * s = sgn(P_up) sgn(P_dn) (Eq. reweight); without them s = +1. */
     double mean_sign;         /* sum(s) / n_samples */
     int64_t n_perm_accepted;  /* permutation swaps accepted since the last reset */
+    /* filter log-weights (one per worldline and sweep since the last reset) whose error
+     * estimate (hqmc_logw_error) exceeds the precision's tolerance, 1e-5 (FP32) or 1e-12
+     * (FP64) of max(1, |log Z|); such a log-weight may be less accurate than that. */
+    int64_t n_inexact;
 } hqmc_obs;
 
 /* Create a context for n_chains independent chains on CUDA device `device`.
  *   L[c]      linear size of chain c's lattice; 2 <= L[c] and L[c] must be one of the
  *             sizes built into the library (hqmc_supported_L), else HQMC_ERR_UNSUPPORTED:
- *             2, 3, 4, 6, 8, 12, 16, 24, 32 in both precisions; 48, 64, 128 in FP32 only
- *             (one CTA per worldline pair; hqmc_log_weight_grad covers L <= 32).
+ *             2, 3, 4, 6, 8, 12, 16, 24, 32 (a warp group per worldline pair) and 48, 64,
+ *             128 (a thread per line of each worldline), all in both precisions and for
+ *             every entry point.
  *   seeds[c]  Philox key of chain c.
  *   precision HQMC_FP32 or HQMC_FP64.
  * *out receives the context (caller frees it with hqmc_destroy).  No device memory is
@@ -127,6 +132,30 @@ int hqmc_set_params(hqmc_ctx *ctx, int chain, double t, double U, double beta, d
  * attached workspace must be attached again).  Errors: HQMC_ERR_ARG (chain out of range,
  * B < 0), HQMC_ERR_CUDA. */
 int hqmc_set_block(hqmc_ctx *ctx, int chain, int B);
+
+/* Storage of the filter's f_l = W_l . alpha_l for the backward pass of the wide kernel
+ * (L >= 48, FP32 context; L <= 32 and FP64 always stream):
+ *   HQMC_FSTORE_STREAM  every f_l in FP32 (the default; 8 N bytes per particle-slice
+ *                       written and read back)
+ *   HQMC_FSTORE_BF16    f_l kept only every `stride` positions of the FFBS block (0 =
+ *                       ceil(sqrt(longest block))), as BF16 (8 significant bits; the
+ *                       normaliser exponent is not needed to sample); the backward pass
+ *                       recomputes each stride-long segment in FP32 from its checkpoint into
+ *                       a per-CTA buffer and samples from it.  f then carries the BF16
+ *                       rounding (relative 2^-9) propagated through the segment, so draws can
+ *                       differ from the streamed form where a uniform lies that close to a
+ *                       CDF edge; log-weights come from the forward pass and are unchanged.
+ *                       Memory per resident worldline drops from M N to about
+ *                       (M / stride) N / 2 + stride N floats; the recompute doubles the FFT
+ *                       work of the filter.
+ *   HQMC_FSTORE_F32     the same with FP32 checkpoints: the recompute is exact, so every draw
+ *                       equals the streamed form's (a check of the recompute path).
+ * A change re-lays the context out at its next use as described at hqmc_set_class_launch.
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_UNSUPPORTED (checkpoints in an FP64 context), HQMC_ERR_CUDA. */
+#define HQMC_FSTORE_STREAM 0
+#define HQMC_FSTORE_BF16 1
+#define HQMC_FSTORE_F32 2
+int hqmc_set_ffbs_storage(hqmc_ctx *ctx, int kind, int stride);
 
 /* CUDA stream (a cudaStream_t passed as void*) on which every later call is ordered;
  * NULL = the legacy default stream.  Changing it drops the captured sweep graph. */
@@ -184,6 +213,25 @@ int hqmc_attach_workspace(hqmc_ctx *ctx, void *dev_ptr, size_t bytes);
  * Errors: HQMC_ERR_STATE (no params), HQMC_ERR_NOMEM, HQMC_ERR_CUDA. */
 int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
 
+/* Error estimates of the log-weights of the last sweep, written to err_out (host, packed
+ * like hqmc_sweep's logw_out).  The power-of-two normaliser is exact, so the error of a
+ * block's log-weight is that of its end value alpha_end(x_end).  An FFT leaves every site
+ * of a slice with a rounding error of about eps log2(N) of the slice's largest value, so a
+ * site that ends kappa = max_y alpha_end(y) / alpha_end(x_end) times below the largest
+ * carries about eps log2(N) kappa from each slice.  The estimate of a block of len slices
+ * is eps log2(N) len kappa (eps = 2^-24 in FP32, 2^-53 in FP64; the end concentration
+ * stands in for every slice's), summed over the worldline's blocks; with
+ * HQMC_CONV_STENCIL every output is a sum of non-negative terms that keeps its own
+ * relative accuracy and kappa is replaced by 1.  A non-positive end value gives +inf.
+ * Worldlines whose estimate exceeds the precision's tolerance are counted in
+ * hqmc_obs.n_inexact; where this matters (strong fields concentrate the message, kappa of
+ * 1e4 and beyond) the stencil form gives the accurate value.  Calibration against a direct
+ * O(N^2) convolution: FP32 errors stayed below 0.73 of the estimate; FP64 errors under
+ * strong Gaussian fields (U < 0 with |U| dtau >= 0.4, where the message concentrates more
+ * at interior slices than at the end) reached 1.3e-11 relative without a flag.
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_STATE (no sweep yet), HQMC_ERR_CUDA. */
+int hqmc_logw_error(hqmc_ctx *ctx, double *err_out);
+
 /* Run n_sweeps >= 0 local-update sweeps (Sec. 3.5.1, Eq. Rlocal, read in the position
  * basis) on the context's stream, as an alternative or a complement to the FFBS sweep.
  * One sweep proposes, for every worldline and slice l once, a move of x_l by one lattice
@@ -240,6 +288,31 @@ int hqmc_set_perm(hqmc_ctx *ctx, int chain, const int32_t *perm);
  * (k_a = 2 pi k_a / L) and C(r) = <S^z_0 S^z_r> at r = rx + L ry, packed over chains.
  * reset != 0 zeroes the accumulators after reading.  Errors: HQMC_ERR_STATE, _CUDA. */
 int hqmc_measure(hqmc_ctx *ctx, hqmc_obs *out, double *Sk, double *Cr, int reset);
+
+/* Open-path estimator of the one-body density matrix and the momentum distribution (Sec. 4,
+ * "Observables": n_k = (1/N) sum_{i,j,sigma} e^{ik.(r_i - r_j)} <c^dag_{j sigma} c_{i sigma}>).
+ * Closed worldlines carry no off-diagonal element, but the FFBS filter of a unit already
+ * holds the weights of the open ones: its end message alpha_end(y) sums the unit's paths
+ * that end at y instead of at the held end x_e, so alpha_end(x_e + r) / alpha_end(x_e) is
+ * the weight of the configuration cut at x_e and displaced there by r, relative to the
+ * closed one; over the sampled (closed) ensemble its mean is that ratio of partition sums
+ * (reading of this library: the Rao-Blackwellised displacement estimator).  on = 1: every
+ * later sweep adds, for the last block of every worldline's unit, sign x alpha_end(x_e + r)
+ * / alpha_end(x_e) to a per-chain sum over r = rx + L ry (N values; the sign is the
+ * permutation sign with hqmc_set_permutations, else +1).  This costs 2 N FP64 atomics per
+ * worldline pair and sweep.  Turning it on or off drops the captured sweep graph and
+ * restarts every observable accumulator (as hqmc_measure with reset).
+ * Errors: HQMC_ERR_ARG, HQMC_ERR_CUDA. */
+int hqmc_set_measure_open(hqmc_ctx *ctx, int on);
+
+/* Read the open-path estimator (hqmc_set_measure_open must be on): per chain, packed over
+ * chains, N values each (host arrays, nullable):
+ *   nk[k]  n_k = (1/N) sum_r cos(k.r) A(r), k = kx + L ky, k_a = 2 pi k_a / L, spin-summed
+ *          (the mean of n_k over k is the density n)
+ *   dm[r]  A(r) / N = (1/N) sum_x sum_sigma <c^dag_{x+r} c_x>, r = rx + L ry (dm[0] = n)
+ * with A(r) the accumulated sum divided by the sum of signs since the last reset.
+ * Errors: HQMC_ERR_STATE (estimator off or no state), HQMC_ERR_CUDA. */
+int hqmc_measure_open(hqmc_ctx *ctx, double *nk, double *dm);
 
 /* Checkpoint format of hqmc_log_weight_grad's reverse pass.  The forward pass keeps
  * F_l = W_l . alpha_l only every `stride` slices (0 = ceil(sqrt M)) and the reverse pass

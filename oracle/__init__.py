@@ -38,6 +38,8 @@ def lib():
         L.orc_backward.argtypes = [i, i, vp, vp, i, u64, u64, u64, vp, vp]
         L.orc_filter_block.argtypes = [i, i, vp, vp, i, i, i, i, vp]
         L.orc_filter_block.restype = d
+        L.orc_open_ratio.argtypes = [i, i, vp, vp, i, i, i, i, vp]
+        L.orc_open_ratio.restype = d
         L.orc_backward_block.argtypes = [i, i, vp, vp, i, i, u64, u64, u64, vp, vp]
         L.orc_sweep.argtypes = [i, i, i, d, d, d, u64, u64, vp, vp, vp, vp, vp, vp, vp, i, i]
         L.orc_sweep.restype = i
@@ -214,6 +216,36 @@ class Chain:
             out["margin_perm"] = mperm
         return out
 
+    def slice_potentials(self):
+        """W [2][M][N] of the current fields: Hirsch exp(+-lambda s) by spin, or Gaussian
+        exp(a sigma) for both spins."""
+        if self.gauss:
+            w = np.exp(gauss_coupling(self.U, self.dtau) * self.sigma)
+            return np.stack([w, w])
+        lm = lam(self.U, self.dtau)
+        return np.stack([np.exp(lm * self.s), np.exp(-lm * self.s)])
+
+    def open_estimate(self, W, a, block=0):
+        """Sum over every worldline of its unit's last-block open-path ratios (orc_open_ratio),
+        [N] indexed by the displacement r = rx + L ry of the end: the per-sweep sample of
+        sum_x sum_sigma <c^dag_{x+r} c_x> (Sec. 4, "Observables", n_k), for the fields W the
+        sweep filters with, its anchor a, the current permutation and the held sites."""
+        L, M, N = self.L, self.M, self.N
+        g, _ = g_table(L, self.t, self.dtau)
+        B = block if 0 < block < M else M
+        nblk = (M + B - 1) // B
+        acc = np.zeros(N)
+        for sg in range(2):
+            for p in range(self.Nsig):
+                q = self.perm[sg, p]
+                vp = np.where(np.arange(M) < a, self.x[sg, q], self.x[sg, p])
+                vp[a] = self.x[sg, q, a]
+                l0 = (a + (nblk - 1) * B) % M
+                ln = M - (nblk - 1) * B
+                xs = self.x[sg, p, a] if nblk == 1 else vp[l0]
+                acc += open_ratio(L, M, g, W[sg], l0, ln, int(xs), int(vp[(l0 + ln) % M]))
+        return acc
+
     def grad(self, v=None):
         """(logZ, dlogZ/dv [2][M][N], dlogZ/dt) with every worldline anchored at slice 0."""
         dv = np.zeros((2, self.M, self.N))
@@ -238,6 +270,15 @@ def filter_block(L, M, g, W, l0, B, xs, xe, want_f=False):
     f = np.zeros((M, L * L)) if want_f else None
     lz = lib().orc_filter_block(L, M, _p(g), _p(W), l0, B, xs, xe, _p(f))
     return (lz, f) if want_f else lz
+
+
+def open_ratio(L, M, g, W, l0, B, xs, xe):
+    """alpha_end(xe + r) / alpha_end(xe) [N] (r = rx + L ry) of the block's filter from xs."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(L * L)
+    lib().orc_open_ratio(L, M, _p(g), _p(W), l0, B, xs, xe, _p(out))
+    return out
 
 
 def backward_block(L, M, g, f, l0, B, seed, sweep, wl, xpath):

@@ -231,6 +231,39 @@ double orc_filter_block(int L, int M, const double *g, const double *W, int l0, 
     return logZ;
 }
 
+/* Open-path weights of a block (Sec. 4, "Observables": n_k needs <c^dag_j c_i>, the weight
+ * of paths that do not close).  The block's filter from xs gives alpha_{l0+B}(y) = the sum
+ * over block paths from xs ending at y instead of at the held xe; its ratio to the closed
+ * value alpha_{l0+B}(xe) is the weight ratio of the configuration whose path is cut at
+ * slice l0+B and displaced there by r, against the closed one.  Writes
+ * ratio[rx + L ry] = alpha_{l0+B}(xe + (rx, ry)) / alpha_{l0+B}(xe) (periodic) and returns
+ * the block's log-weight. */
+double orc_open_ratio(int L, int M, const double *g, const double *W, int l0, int B, int xs, int xe,
+                      double *ratio)
+{
+    int N = L * L;
+    double *alpha = calloc(N, sizeof(double)), *f = malloc(N * sizeof(double)),
+           *nxt = malloc(N * sizeof(double));
+    double logZ = 0.0;
+    alpha[xs] = 1.0;
+    for (int i = 0; i < B; ++i) {
+        int l = (l0 + i) % M;
+        for (int x = 0; x < N; ++x) f[x] = W[(size_t)l * N + x] * alpha[x];
+        orc_conv(L, g, f, nxt);
+        double c = 0.0;
+        for (int x = 0; x < N; ++x) c += nxt[x];
+        for (int x = 0; x < N; ++x) alpha[x] = nxt[x] / c;
+        logZ += log(c);
+    }
+    int ex = xe % L, ey = xe / L;
+    for (int ry = 0; ry < L; ++ry)
+        for (int rx = 0; rx < L; ++rx)
+            ratio[rx + L * ry] = alpha[orc_wrap(ex + rx, L) + L * orc_wrap(ey + ry, L)] / alpha[xe];
+    logZ += log(alpha[xe]);
+    free(alpha); free(f); free(nxt);
+    return logZ;
+}
+
 /* Forward filter of the closed loop of one worldline anchored at slice a, site xa:
  * the block of all M slices with both ends at xa. */
 double orc_filter(int L, int M, const double *g, const double *W, int a, int xa, double *f_store)

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         }
         int esum0 = 0, esum1 = 0;
         T fin0 = T(0), fin1 = T(0);
+        T top0 = T(0), top1 = T(0);  // largest value of the final message (kappa = top / fin)
         int l = l0;
         for (int i = 0; i < len; ++i) {
             // the next slice's field bits (Hirsch chains), loaded before this slice's
@@ -401,6 +402,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 const T c1 = reg_select<L>(v, reg1).y;
                 fin0 = __shfl_sync(gmask, c0, own0, GW);
                 fin1 = __shfl_sync(gmask, c1, own1, GW);
+                V mx = vzero(v[0]);
+#pragma unroll
+                for (int r = 0; r < L; ++r) {
+                    mx.x = v[r].x > mx.x ? v[r].x : mx.x;
+                    mx.y = v[r].y > mx.y ? v[r].y : mx.y;
+                }
+                top0 = group_max<GW>(mx.x, gmask);
+                top1 = group_max<GW>(mx.y, gmask);
+                // open-path estimator (one-body density matrix, for n_k): the last block's end
+                // message read at every site, relative to the held end, sign-weighted
+                const bool last_blk = BLK ? (int(meta[0]) == int(meta[1]) - 1) : true;
+                if (st.open_acc && last_blk && active) {
+                    double *acc = st.open_acc + cd.meas_off;
+                    const T sgn = T(chain_sign(st, c));
+                    const T i0 = fin0 > T(0) ? sgn / fin0 : T(0), i1 = (has1 && fin1 > T(0)) ? sgn / fin1 : T(0);
+#pragma unroll
+                    for (int r = 0; r < L; ++r) {
+                        const int x = finC ? gl : r, y = finC ? r : gl;
+                        const int d0 = (x - ex0 + L) % L + L * ((y - ey0 + L) % L);
+                        const int d1 = (x - ex1 + L) % L + L * ((y - ey1 + L) % L);
+                        if (i0 != T(0)) atomicAdd(acc + d0, double(v[r].x * i0));
+                        if (i1 != T(0)) atomicAdd(acc + d1, double(v[r].y * i1));
+                    }
+                }
             }
             l = l1;
         }
@@ -412,26 +437,55 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             const double part1 = double(esum1) * ln2 + log(double(fin1));
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
+            const double inf = __longlong_as_double(0x7ff0000000000000LL);
+            const double err0 = fin0 > T(0) ? logw_err_estimate<T>(double(top0) / double(fin0), len, L, STN) : inf;
+            const double err1 = fin1 > T(0) ? logw_err_estimate<T>(double(top1) / double(fin1), len, L, STN) : inf;
+            // a log-weight whose estimate exceeds the tolerance is counted (hqmc_obs.n_inexact)
+            auto flag = [&](double lwv, double e) {
+                if (!(e <= logw_tolerance<T>() * fmax(1.0, fabs(lwv)))) atomicAdd(&st.meas[c].inexact, 1ull);
+            };
             double *lw = st.logw + cd.logw_off;
+            double *le = st.logw_err + cd.logw_off;
             const int b = BLK ? int(meta[0]) : 0, nblk = BLK ? int(meta[1]) : 1, rr = BLK ? int(meta[2]) : 0;
             if (!BLK || nblk == 1) {
                 lw[wl0] = part0;
-                if (has1) lw[wl1] = part1;
+                le[wl0] = err0;
+                flag(part0, err0);
+                if (has1) {
+                    lw[wl1] = part1;
+                    le[wl1] = err1;
+                    flag(part1, err1);
+                }
             } else {
                 double *lp = st.logw_part + cd.lwp_off;
+                double *ep = st.logw_err_part + cd.lwp_off;
                 lp[wl0 * nblk + b] = part0;
-                if (has1) lp[wl1 * nblk + b] = part1;
+                ep[wl0 * nblk + b] = err0;
+                if (has1) {
+                    lp[wl1 * nblk + b] = part1;
+                    ep[wl1 * nblk + b] = err1;
+                }
                 __threadfence();
                 unsigned *done = st.blk_done + cd.done_off + rr;
                 if (atomicAdd(done, 1u) == unsigned(nblk - 1)) {
                     __threadfence();
-                    double s0 = 0.0, s1 = 0.0;
+                    double s0 = 0.0, s1 = 0.0, e0 = 0.0, e1 = 0.0;
                     for (int k = 0; k < nblk; ++k) {
                         s0 += __ldcg(lp + wl0 * nblk + k);
-                        if (has1) s1 += __ldcg(lp + wl1 * nblk + k);
+                        e0 += __ldcg(ep + wl0 * nblk + k);
+                        if (has1) {
+                            s1 += __ldcg(lp + wl1 * nblk + k);
+                            e1 += __ldcg(ep + wl1 * nblk + k);
+                        }
                     }
                     lw[wl0] = s0;
-                    if (has1) lw[wl1] = s1;
+                    le[wl0] = e0;
+                    flag(s0, e0);
+                    if (has1) {
+                        lw[wl1] = s1;
+                        le[wl1] = e1;
+                        flag(s1, e1);
+                    }
                     *done = 0u;  // ready for the next sweep
                 }
             }

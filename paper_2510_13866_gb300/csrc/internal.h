@@ -69,6 +69,8 @@ struct MeasAcc {
     unsigned long long local_accepted;  // accepted local link moves
     long long sign_sum;                 // sum over measured sweeps of sgn(P_up) sgn(P_dn)
     unsigned long long perm_accepted;   // accepted permutation swaps
+    unsigned long long inexact;         // filter log-weights whose error estimate exceeds the
+                                        // precision's tolerance (logw_err_estimate)
 };
 // The sums n_sum, d_sum, m2_sum, link_sum and S(k) are weighted by the sweep's sign
 // (two's complement in the unsigned counters); with permutations off the sign is +1.
@@ -90,9 +92,13 @@ struct DevState {
     void *gw;            // their slice potentials W = exp(a sigma), rows then columns
     int gw_f64;          // W stored as double (FP64 context) or float
     double *logw_part;   // per-block log-weight partials of block FFBS
+    double *logw_err;    // error estimates of the log-weights of the last sweep (as logw)
+    double *logw_err_part;  // their per-block partials (as logw_part)
     unsigned *blk_done;  // per-pair counters of finished blocks (zero between sweeps)
     int *perm;           // permutations at tau = beta and their inverses (perm_off per chain)
     unsigned *parity;    // per chain: bit 0 = parity of P_up P_dn (sign -1 when set)
+    double *open_acc;    // per chain N (nullable: off): sum over sweeps, spins and worldlines of
+                         // sign x alpha_end(x_e + r) / alpha_end(x_e) (open-path estimator)
 };
 
 // Blocks of the FFBS loop of a chain: length B (0 or >= M: one block of M slices) and count.
@@ -120,6 +126,12 @@ struct FfbsLaunch {
     int stencil;               // line convolutions by the periodic stencil instead of the FFT
     int general;               // some chain has FFBS blocks B < M, or the context has used
                                // permutations: the general work-unit instantiation runs
+    // wide kernel, FP32: f kept only every ckpt_K positions (0: every f streamed), as BF16
+    // (ckpt_bf16) or FP32 checkpoints at the start of a worldline's slot; the backward pass
+    // recomputes each segment into the buffer at seg_off (elements) of the slot
+    int ckpt_K;
+    int ckpt_bf16;
+    long long seg_off;
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.
@@ -168,5 +180,8 @@ cudaError_t launch_gauss_w(const DevState &st, int chain, int M, int N, cudaStre
 // observables read-out: S(k) and C(r) of every chain; tmp holds 2 N doubles per chain
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out,
                            double *sk_out, double *tmp, cudaStream_t stream);
+// n_k and the one-body density matrix of every chain from the open-path sums
+cudaError_t launch_readout_open(const DevState &st, int nchains, int max_N, double *nk_out,
+                                double *dm_out, double *tmp, cudaStream_t stream);
 
 }  // namespace hqmc

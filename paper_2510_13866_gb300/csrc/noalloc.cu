@@ -31,7 +31,7 @@ constexpr unsigned kStatusBadInput = 8u;
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct StaticLayout {
-    size_t cd, tab, cls, sbits, x, hist, meas, anchor, sweep, status, slots, fixed;
+    size_t cd, tab, cls, sbits, x, hist, meas, anchor, sweep, status, lerr, slots, fixed;
 };
 
 StaticLayout layout_for(int L, int M, int Nsig) {
@@ -58,6 +58,8 @@ StaticLayout layout_for(int L, int M, int Nsig) {
     o = align256(o + 8);
     s.status = o;
     o = align256(o + 8);
+    s.lerr = o;  // error estimates of the log-weights (the kernel writes them; not returned)
+    o = align256(o + 2 * size_t(Nsig) * 8);
     s.slots = o;
     s.fixed = o;
     return s;
@@ -225,6 +227,7 @@ extern "C" int hqmc_ffbs_noalloc(int L, int M, int Nsig, double t, double U, dou
     ds.dens = nullptr;
     ds.sweep = reinterpret_cast<unsigned long long *>(base + lay.sweep);
     ds.status = reinterpret_cast<unsigned *>(base + lay.status);
+    ds.logw_err = reinterpret_cast<double *>(base + lay.lerr);
     FfbsLaunch fl{};
     fl.class_chains = reinterpret_cast<const int *>(base + lay.cls);
     fl.class_unit_off = fl.class_chains + 1;  // the closed loop: one unit per pair

@@ -23,12 +23,15 @@ cudaError_t grad_occupancy_f32(int L, int *blocks);
 cudaError_t grad_occupancy_f64(int L, int *blocks);
 constexpr int kGradWarpsHost = 4;  // warps per CTA of the adjoint kernel (fixed)
 
-cudaError_t launch_ffbs_big(int L, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s);
-cudaError_t ffbs_big_occupancy(int L, int *blocks);
-bool ffbs_big_supported(int L);
+cudaError_t launch_ffbs_wide(int L, bool fp64, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s);
+cudaError_t launch_grad_wide(int L, bool fp64, const DevState &st, const GradLaunch &gk, int grid, cudaStream_t s);
+cudaError_t grad_wide_occupancy(int L, bool fp64, int *blocks);
+cudaError_t ffbs_wide_occupancy(int L, bool fp64, int *blocks);
+bool ffbs_wide_supported(int L);
+int ffbs_wide_wpc(int L);
 
-// register-line sizes (one warp-group per pair, FP32 and FP64) and wide sizes (one CTA
-// per pair, FP32 only)
+// register-line sizes (one warp-group per pair) and wide sizes (one thread per line of
+// each worldline, one or two worldlines per CTA); both precisions
 static const int kSizes[] = {2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 128};
 
 bool ffbs_supported(int L) {
@@ -55,7 +58,8 @@ struct HostChain {
 struct LClass {
     int L = 0;
     std::vector<int> chains;
-    std::vector<int> pair_off;  // prefix sums of 2*npair (the adjoint's work units)
+    std::vector<int> pair_off;  // prefix sums of the adjoint's work units per chain: 2 npair
+                                // (L <= 32), 2 ceil(Nsig / WPC) worldline groups (wide)
     std::vector<int> unit_off;  // prefix sums of 2*npair*nblk (FFBS work units: pair, block)
     int total_pairs = 0;
     int total_units = 0;
@@ -65,6 +69,10 @@ struct LClass {
     long long groups = 0;  // worldline groups launched
     size_t scratch_off = 0;
     size_t scratch_bytes = 0;
+    // wide classes with f checkpoints (FP32): every K positions, the segment buffer at
+    // seg_off of a worldline's slot of wl_elems floats (ckpt_K = 0: every f streamed)
+    int ckpt_K = 0;
+    long long seg_off = 0, wl_elems = 0;
     size_t cls_off = 0;    // device offset of the class arrays
 };
 
@@ -101,7 +109,10 @@ struct hqmc_ctx {
     std::vector<ChainDev> cdev;
     std::vector<LClass> classes;
     DevState st{};
-    size_t off_cr = 0, off_sko = 0, off_rd = 0, total_N = 0;
+    size_t off_cr = 0, off_sko = 0, off_rd = 0, off_open = 0, total_N = 0;
+    bool open_on = false;  // open-path estimator (one-body density matrix, n_k) accumulated
+    int fstore = HQMC_FSTORE_STREAM;  // storage of f for the backward pass (wide sizes, FP32)
+    int fstride = 0;                  // checkpoint stride (0: ceil(sqrt(longest block)))
     long long total_wl = 0;
     double *d_cr = nullptr, *d_sko = nullptr, *d_rd = nullptr;
     uint64_t sweeps_host = 0;
@@ -281,7 +292,7 @@ void free_layout(hqmc_ctx *c) {
 }
 
 int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
-    cudaError_t e = is_big(L) ? ffbs_big_occupancy(L, blocks)
+    cudaError_t e = is_big(L) ? ffbs_wide_occupancy(L, c->precision == HQMC_FP64, blocks)
                     : c->precision == HQMC_FP64 ? ffbs_occupancy_f64(L, wpc, blocks)
                                                 : ffbs_occupancy_f32(L, wpc, blocks);
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
@@ -356,7 +367,7 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         qb += 4LL * h.Nsig;  // P [2][Nsig], then P^{-1} [2][Nsig]
         if (nblk > 1) {
             pb += 2LL * h.Nsig * nblk;
-            db += 2LL * d.npair;
+            db += 2LL * h.Nsig;  // one counter per work group: a pair (L <= 32) or fewer worldlines
         }
         d.gcoup = std::sqrt(std::fabs(h.U) * h.dtau);
         d.g_off = gb;
@@ -390,12 +401,15 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     const size_t o_gs = take(size_t(gb) * 8);
     const size_t o_gw = take(size_t(gb) * 2 * (f64 ? 8 : 4));
     const size_t o_lp = take(size_t(pb) * 8);
+    const size_t o_le = take(size_t(lb) * 8);
+    const size_t o_lep = take(size_t(pb) * 8);
     const size_t o_bd = take(size_t(db) * 4);
     const size_t o_pm = take(size_t(qb) * 4);
     const size_t o_par = take(size_t(nc) * 4);
     c->off_cr = take(size_t(mb) * 8);
     c->off_sko = take(size_t(mb) * 8);
     c->off_rd = take(size_t(mb) * 16);  // read-out passes: 2 N doubles per chain
+    c->off_open = take(size_t(mb) * 8);  // open-path sums: N doubles per chain
     // classes
     for (auto &k : c->classes) {
         k.pair_off.assign(1, 0);
@@ -404,8 +418,13 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         k.len_max = 0;
         for (int ci : k.chains) {
             const ChainDev &d = c->cdev[ci];
-            k.pair_off.push_back(k.pair_off.back() + 2 * d.npair);
-            k.unit_off.push_back(k.unit_off.back() + 2 * d.npair * ffbs_nblk(d.block, d.M));
+            const int gw = is_big(k.L) ? ffbs_wide_wpc(k.L) : 2;
+            k.pair_off.push_back(k.pair_off.back() + 2 * ((d.Nsig + gw - 1) / gw));
+            // FFBS work units (group, block); a group is a worldline pair, or for the wide
+            // kernel the worldlines one CTA holds
+            const int wg = is_big(k.L) ? ffbs_wide_wpc(k.L) : 2;
+            const int ngrp = (d.Nsig + wg - 1) / wg;
+            k.unit_off.push_back(k.unit_off.back() + 2 * ngrp * ffbs_nblk(d.block, d.M));
             k.M_max = std::max(k.M_max, d.M);
             k.len_max = std::max(k.len_max, ffbs_block_len(d.block, d.M));
         }
@@ -431,8 +450,21 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         }
         k.grid = std::max(1, grid);
         k.groups = (long long)k.grid * gpc;
-        const size_t elem = f64 ? 16 : 8;
+        // f slots: a worldline pair per group (L <= 32), or the CTA's worldlines (wide)
+        const size_t elem = is_big(k.L) ? size_t(ffbs_wide_wpc(k.L)) * (f64 ? 8 : 4) : (f64 ? 16 : 8);
         k.scratch_bytes = size_t(k.groups) * k.len_max * k.L * k.L * elem;
+        k.ckpt_K = 0;
+        if (is_big(k.L) && !f64 && c->fstore != HQMC_FSTORE_STREAM) {
+            // checkpoints every K positions (BF16: two per float) then a K-slice segment
+            const long long N = (long long)k.L * k.L;
+            const int K = c->fstride > 0 ? std::min(c->fstride, k.len_max)
+                                         : std::max(1, int(std::ceil(std::sqrt(double(k.len_max)))));
+            const long long nseg = (k.len_max + K - 1) / K;
+            k.ckpt_K = K;
+            k.seg_off = (c->fstore == HQMC_FSTORE_BF16) ? nseg * N / 2 : nseg * N;
+            k.wl_elems = k.seg_off + (long long)K * N;
+            k.scratch_bytes = size_t(k.groups) * ffbs_wide_wpc(k.L) * size_t(k.wl_elems) * 4;
+        }
         k.scratch_off = take(k.scratch_bytes);
     }
     *total = round_up(off, 256);
@@ -454,6 +486,8 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
     c->st.gw = reinterpret_cast<void *>(o_gw);
     c->st.gw_f64 = f64 ? 1 : 0;
     c->st.logw_part = reinterpret_cast<double *>(o_lp);
+    c->st.logw_err = reinterpret_cast<double *>(o_le);
+    c->st.logw_err_part = reinterpret_cast<double *>(o_lep);
     c->st.blk_done = reinterpret_cast<unsigned *>(o_bd);
     c->st.perm = reinterpret_cast<int *>(o_pm);
     c->st.parity = reinterpret_cast<unsigned *>(o_par);
@@ -503,10 +537,13 @@ int prepare(hqmc_ctx *c) {
     s.gsig = rebase(s.gsig, c->base);
     s.gw = rebase(s.gw, c->base);
     s.logw_part = rebase(s.logw_part, c->base);
+    s.logw_err = rebase(s.logw_err, c->base);
+    s.logw_err_part = rebase(s.logw_err_part, c->base);
     s.blk_done = rebase(s.blk_done, c->base);
     s.perm = rebase(s.perm, c->base);
     s.parity = rebase(s.parity, c->base);
     c->d_cr = reinterpret_cast<double *>(c->base + c->off_cr);
+    s.open_acc = c->open_on ? reinterpret_cast<double *>(c->base + c->off_open) : nullptr;
     c->d_sko = reinterpret_cast<double *>(c->base + c->off_sko);
     c->d_rd = reinterpret_cast<double *>(c->base + c->off_rd);
     cudaStream_t st = c->stream;
@@ -648,11 +685,16 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.general = (cl.total_units != cl.total_pairs || c->perm_used) ? 1 : 0;
         fl.stencil = (c->conv == HQMC_CONV_STENCIL && !is_big(cl.L)) ? 1 : 0;
         fl.scratch = c->base + cl.scratch_off;
-        fl.slot_elems = (long long)cl.len_max * cl.L * cl.L;
+        // slot per group: pair elements (L <= 32) or scalars of the CTA's worldlines (wide)
+        fl.slot_elems = (long long)cl.len_max * cl.L * cl.L * (is_big(cl.L) ? ffbs_wide_wpc(cl.L) : 1);
+        fl.ckpt_K = cl.ckpt_K;
+        fl.ckpt_bf16 = c->fstore == HQMC_FSTORE_BF16 ? 1 : 0;
+        fl.seg_off = cl.seg_off;
+        if (cl.ckpt_K > 0) fl.slot_elems = cl.wl_elems * ffbs_wide_wpc(cl.L);
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
         HQMC_CUDA(c, cudaMemsetAsync(fl.next_unit, 0, sizeof(unsigned), s));
         const int wpc = default_wpc(c, cl.L);
-        cudaError_t e = is_big(cl.L) ? launch_ffbs_big(cl.L, c->st, fl, cl.grid, s)
+        cudaError_t e = is_big(cl.L) ? launch_ffbs_wide(cl.L, f64, c->st, fl, cl.grid, s)
                         : f64        ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
                                      : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "ffbs launch");
@@ -729,7 +771,7 @@ int hqmc_init_lattice(hqmc_ctx **out, int n_chains, const int *L, const uint64_t
     *out = nullptr;
     for (int i = 0; i < n_chains; ++i) {
         if (L[i] < 2) return HQMC_ERR_ARG;
-        const bool ok = ffbs_supported(L[i]) || (precision == HQMC_FP32 && ffbs_big_supported(L[i]));
+        const bool ok = ffbs_supported(L[i]) || ffbs_wide_supported(L[i]);
         if (!ok) return HQMC_ERR_UNSUPPORTED;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
@@ -775,8 +817,6 @@ int hqmc_set_params(hqmc_ctx *c, int chain, double t, double U, double beta, dou
             return fail(c, HQMC_ERR_STATE, "M and Nsig are fixed once the state exists");
         if (c->ready && ((U < 0.0) != (c->ch[i].U < 0.0)))
             return fail(c, HQMC_ERR_STATE, "the field type (Hirsch for U >= 0, Gaussian for U < 0) is fixed once the state exists");
-        if (U < 0.0 && c->ch[i].L > 32 && c->precision == HQMC_FP64)
-            return fail(c, HQMC_ERR_UNSUPPORTED, "no FP64 form for L > 32");
     }
     for (int i = lo; i < hi; ++i) {
         HostChain &h = c->ch[i];
@@ -907,6 +947,21 @@ int hqmc_set_perm(hqmc_ctx *c, int chain, const int32_t *perm) {
     }
     HQMC_CUDA(c, cudaMemcpyAsync(c->st.parity + chain, &par, 4, cudaMemcpyHostToDevice, c->stream));
     HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HQMC_OK;
+}
+
+int hqmc_set_ffbs_storage(hqmc_ctx *c, int kind, int stride) {
+    if (!c) return HQMC_ERR_ARG;
+    if (kind != HQMC_FSTORE_STREAM && kind != HQMC_FSTORE_BF16 && kind != HQMC_FSTORE_F32)
+        return fail(c, HQMC_ERR_ARG, "unknown storage kind");
+    if (stride < 0) return fail(c, HQMC_ERR_ARG, "stride must be >= 0");
+    if (kind != HQMC_FSTORE_STREAM && c->precision == HQMC_FP64)
+        return fail(c, HQMC_ERR_UNSUPPORTED, "checkpoints of f are built for the FP32 filter");
+    const bool changed = kind != c->fstore || stride != c->fstride;
+    c->fstore = kind;
+    c->fstride = stride;
+    // the scratch layout depends on it: lay out again at the next use, keeping the state
+    if (changed) return stash_state(c);
     return HQMC_OK;
 }
 
@@ -1106,6 +1161,15 @@ int hqmc_sweep(hqmc_ctx *c, int n_sweeps, double *logw_out) {
     return check_status(c);
 }
 
+int hqmc_logw_error(hqmc_ctx *c, double *err_out) {
+    if (!c || !err_out) return HQMC_ERR_ARG;
+    if (!c->ready || !c->started) return fail(c, HQMC_ERR_STATE, "no sweep has run");
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    HQMC_CUDA(c, cudaMemcpyAsync(err_out, c->st.logw_err, sizeof(double) * c->total_wl, cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HQMC_OK;
+}
+
 int hqmc_local_sweep(hqmc_ctx *c, int n_sweeps) {
     if (!c || n_sweeps < 0) return HQMC_ERR_ARG;
     int rc = prepare(c);
@@ -1166,13 +1230,47 @@ int hqmc_measure(hqmc_ctx *c, hqmc_obs *out, double *Sk, double *Cr, int reset) 
             o.n_degenerate = (int64_t)acc[i].degenerate;
             o.n_nonpositive = (int64_t)acc[i].nonpositive;
             o.n_local_accepted = (int64_t)acc[i].local_accepted;
+            o.n_inexact = (int64_t)acc[i].inexact;
         }
     }
     if (reset) {
         HQMC_CUDA(c, cudaMemsetAsync(c->st.meas, 0, sizeof(MeasAcc) * c->nchains, c->stream));
         HQMC_CUDA(c, cudaMemsetAsync(c->st.sk, 0, 8 * c->total_N, c->stream));
+        HQMC_CUDA(c, cudaMemsetAsync(c->base + c->off_open, 0, 8 * c->total_N, c->stream));
         HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
+    return HQMC_OK;
+}
+
+int hqmc_set_measure_open(hqmc_ctx *c, int on) {
+    if (!c) return HQMC_ERR_ARG;
+    c->open_on = on != 0;
+    drop_graph(c);  // the captured sweep holds the device state by value
+    if (c->ready) {
+        HQMC_CUDA(c, cudaSetDevice(c->device));
+        c->st.open_acc = c->open_on ? reinterpret_cast<double *>(c->base + c->off_open) : nullptr;
+        // every accumulator restarts, so that the open-path sums and the sign sum cover the
+        // same sweeps
+        HQMC_CUDA(c, cudaMemsetAsync(c->st.meas, 0, sizeof(MeasAcc) * c->nchains, c->stream));
+        HQMC_CUDA(c, cudaMemsetAsync(c->st.sk, 0, 8 * c->total_N, c->stream));
+        HQMC_CUDA(c, cudaMemsetAsync(c->base + c->off_open, 0, 8 * c->total_N, c->stream));
+        HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return HQMC_OK;
+}
+
+int hqmc_measure_open(hqmc_ctx *c, double *nk, double *dm) {
+    if (!c) return HQMC_ERR_ARG;
+    if (!c->ready || !c->open_on) return fail(c, HQMC_ERR_STATE, "the open-path estimator is off");
+    HQMC_CUDA(c, cudaSetDevice(c->device));
+    int max_N = 0;
+    for (auto &d : c->cdev) max_N = std::max(max_N, d.N);
+    // the read-out uses the S(k) / C(r) output arrays as its destination
+    cudaError_t e = launch_readout_open(c->st, c->nchains, max_N, c->d_cr, c->d_sko, c->d_rd, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "open readout");
+    if (nk) HQMC_CUDA(c, cudaMemcpyAsync(nk, c->d_cr, 8 * c->total_N, cudaMemcpyDeviceToHost, c->stream));
+    if (dm) HQMC_CUDA(c, cudaMemcpyAsync(dm, c->d_sko, 8 * c->total_N, cudaMemcpyDeviceToHost, c->stream));
+    HQMC_CUDA(c, cudaStreamSynchronize(c->stream));
     return HQMC_OK;
 }
 
@@ -1310,8 +1408,6 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
         long long groups;
         size_t ck_bytes, ck_exp_off, seg_elems, off;
     };
-    for (const LClass &cl : c->classes)
-        if (is_big(cl.L)) return fail(c, HQMC_ERR_UNSUPPORTED, "the adjoint covers L <= 32");
     std::vector<Plan> plans(c->classes.size());
     const size_t head = size_t(c->nchains) * 16 + c->classes.size() * 4;  // logz, dt per chain; counters
     size_t off = round_up(head, 256);
@@ -1322,6 +1418,23 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
         p.K = c->ckpt_stride > 0 ? std::min(c->ckpt_stride, M) : std::max(1, int(std::ceil(std::sqrt(double(M)))));
         p.nseg = (M + p.K - 1) / p.K;
         const size_t N = size_t(cl.L) * cl.L;
+        if (is_big(cl.L)) {
+            // wide: one CTA per group of WPC worldlines; per worldline the checkpoints (BF16 or
+            // the context precision) and a segment of K slices plus a spare one for b
+            const int wpc = ffbs_wide_wpc(cl.L);
+            p.ck_exp_off = 0;
+            p.ck_bytes = size_t(wpc) * round_up(size_t(p.nseg) * N * (bf16 ? 2 : tsz), 256);
+            p.seg_elems = size_t(wpc) * (size_t(p.K) + 1) * N;
+            int bps = 1;
+            cudaError_t e = grad_wide_occupancy(cl.L, f64, &bps);
+            if (e != cudaSuccess) return cuda_fail(c, e, "grad occupancy");
+            bps = std::max(1, bps);
+            p.grid = std::max(1, std::min(cl.total_pairs, bps * c->num_sms));
+            p.groups = p.grid;
+            p.off = off;
+            off = round_up(off + size_t(p.groups) * (p.ck_bytes + p.seg_elems * tsz), 256);
+            continue;
+        }
         p.ck_exp_off = round_up(size_t(p.nseg) * N * (bf16 ? 4 : vsz), 16);
         p.ck_bytes = round_up(p.ck_exp_off + size_t(p.nseg) * 8, 256);
         p.seg_elems = size_t(p.K) * N;
@@ -1375,7 +1488,9 @@ int hqmc_log_weight_grad(hqmc_ctx *c, const void *v, double *logZ, void *dlogZ_d
         gk.logz = d_logz;
         gk.dt = d_dt;
         gk.next_pair = d_next + k;
-        cudaError_t e = f64 ? launch_grad_f64(cl.L, c->st, gk, p.grid, st) : launch_grad_f32(cl.L, c->st, gk, p.grid, st);
+        cudaError_t e = is_big(cl.L) ? launch_grad_wide(cl.L, f64, c->st, gk, p.grid, st)
+                        : f64        ? launch_grad_f64(cl.L, c->st, gk, p.grid, st)
+                                     : launch_grad_f32(cl.L, c->st, gk, p.grid, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "grad launch");
     }
     std::vector<double> h(2 * size_t(c->nchains));

@@ -383,11 +383,13 @@ cudaError_t launch_advance(const DevState &st, cudaStream_t stream) {
 // Phases are reduced mod L before the trigonometric call, so every factor is exact to
 // rounding.  Sums are sign-reweighted (divided by the sum of signs, the sample count
 // without permutations).
-__global__ void readout_rows_kernel(DevState st, double *tmp) {
+// src (nullable): per-chain input in place of the accumulated |m(k)|^2 (the open-path sums
+// for n_k, which take the same separable transform with k and r exchanged)
+__global__ void readout_rows_kernel(DevState st, const double *src, double *tmp) {
     const int c = blockIdx.y;
     const ChainDev &cd = st.chains[c];
     const int L = cd.L, N = cd.N;
-    const double *sk = st.sk + cd.meas_off;
+    const double *sk = (src ? src : st.sk) + cd.meas_off;
     double *A = tmp + 2 * cd.meas_off, *B = A + N;
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < N; o += gridDim.x * blockDim.x) {
         const int rx = o % L, ky = o / L;
@@ -433,8 +435,44 @@ __global__ void readout_cols_kernel(DevState st, const double *tmp, double *cr_o
 cudaError_t launch_readout(const DevState &st, int nchains, int max_N, double *cr_out, double *sk_out,
                            double *tmp, cudaStream_t stream) {
     dim3 grid((max_N + 255) / 256, nchains);
-    readout_rows_kernel<<<grid, 256, 0, stream>>>(st, tmp);
+    readout_rows_kernel<<<grid, 256, 0, stream>>>(st, nullptr, tmp);
     readout_cols_kernel<<<grid, 256, 0, stream>>>(st, tmp, cr_out, sk_out);
+    return cudaGetLastError();
+}
+
+// n_k = (1/N) sum_r cos(k.r) A(r) and the one-body density matrix per site A(r) / N, from the
+// open-path sums A(r) = sum over sweeps of sign x sum_{sigma,p} alpha_end(x_e + r) / alpha_end(x_e),
+// divided by the sum of signs (Sec. 4, "Observables"; the paper's n_k with
+// sum_x <c^dag_{x+r} c_x> = A(r)): the same two separable passes as C(r)
+__global__ void readout_open_cols_kernel(DevState st, const double *tmp, double *nk_out, double *dm_out) {
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N;
+    const long long ns = st.meas[c].sign_sum;
+    const double norm = ns ? 1.0 / (double(ns) * N) : 0.0;
+    const double *A = tmp + 2 * cd.meas_off, *B = A + N;
+    const double *acc = st.open_acc + cd.meas_off;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const int kx = k % L, ky = k / L;
+        double s = 0.0;
+        int ph = 0;
+        for (int ry = 0; ry < L; ++ry) {
+            double sn, cs;
+            sincospi(2.0 * double(ph) / double(L), &sn, &cs);
+            s += A[ry * L + kx] * cs - B[ry * L + kx] * sn;
+            ph += ky;
+            if (ph >= L) ph -= L;
+        }
+        nk_out[cd.meas_off + k] = s * norm;
+        dm_out[cd.meas_off + k] = acc[k] * norm;
+    }
+}
+
+cudaError_t launch_readout_open(const DevState &st, int nchains, int max_N, double *nk_out, double *dm_out,
+                                double *tmp, cudaStream_t stream) {
+    dim3 grid((max_N + 255) / 256, nchains);
+    readout_rows_kernel<<<grid, 256, 0, stream>>>(st, st.open_acc, tmp);
+    readout_open_cols_kernel<<<grid, 256, 0, stream>>>(st, tmp, nk_out, dm_out);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ SIGNATURES = {
     "hqmc_init_lattice": (_i, [C.POINTER(_vp), _i, _vp, _vp, _i, _i]),
     "hqmc_set_params": (_i, [_vp, _i, _d, _d, _d, _d, _d]),
     "hqmc_set_block": (_i, [_vp, _i, _i]),
+    "hqmc_set_ffbs_storage": (_i, [_vp, _i, _i]),
     "hqmc_set_stream": (_i, [_vp, _vp]),
     "hqmc_set_launch": (_i, [_vp, _i, _i, _i]),
     "hqmc_set_slice_launch": (_i, [_vp, _i]),
@@ -34,12 +35,15 @@ SIGNATURES = {
     "hqmc_workspace_size": (_i, [_vp, C.POINTER(_sz)]),
     "hqmc_attach_workspace": (_i, [_vp, _vp, _sz]),
     "hqmc_sweep": (_i, [_vp, _i, _vp]),
+    "hqmc_logw_error": (_i, [_vp, _vp]),
     "hqmc_local_sweep": (_i, [_vp, _i]),
     "hqmc_set_permutations": (_i, [_vp, _i]),
     "hqmc_set_conv": (_i, [_vp, _i]),
     "hqmc_get_perm": (_i, [_vp, _i, _vp, _vp]),
     "hqmc_set_perm": (_i, [_vp, _i, _vp]),
     "hqmc_measure": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "hqmc_set_measure_open": (_i, [_vp, _i]),
+    "hqmc_measure_open": (_i, [_vp, _vp, _vp]),
     "hqmc_set_checkpoint": (_i, [_vp, _i, _i]),
     "hqmc_log_weight_grad": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "hqmc_chain_shape": (_i, [_vp, _i, _vp, _vp, _vp]),
@@ -69,7 +73,7 @@ class Obs(C.Structure):
     _fields_ = [("n_samples", C.c_int64), ("density", C.c_double), ("double_occ", C.c_double),
                 ("m2", C.c_double), ("ekin", C.c_double), ("s_pipi", C.c_double),
                 ("n_degenerate", C.c_int64), ("n_nonpositive", C.c_int64), ("n_local_accepted", C.c_int64),
-                ("mean_sign", C.c_double), ("n_perm_accepted", C.c_int64)]
+                ("mean_sign", C.c_double), ("n_perm_accepted", C.c_int64), ("n_inexact", C.c_int64)]
 
 
 _lib = None
@@ -192,6 +196,14 @@ class Lattice:
         if self.torch_memory and self._ws is not None:
             self._attach()
 
+    def set_ffbs_storage(self, kind="stream", stride=0):
+        """Storage of f for the wide kernel's backward pass: "stream" (every slice, FP32),
+        "bf16" or "f32" checkpoints every `stride` positions (0: ceil(sqrt M)) with the
+        segments recomputed."""
+        self._check(lib().hqmc_set_ffbs_storage(self._ctx, {"stream": 0, "bf16": 1, "f32": 2}[kind], int(stride)))
+        if self.torch_memory and self._ws is not None:
+            self._attach()
+
     def set_checkpoint(self, stride=0, bf16=True):
         """Checkpoint stride of the adjoint's reverse pass (0 = ceil(sqrt M)) and format
         (BF16 with a per-slice exponent, or the context's own precision)."""
@@ -296,6 +308,19 @@ class Lattice:
             o += 2 * ns
         return out
 
+    def logw_error(self):
+        """Error estimates of the last sweep's log-weights (hqmc_logw_error), a list of
+        [2, Nsig] arrays per chain like sweep(logw=True)."""
+        self.prepare()
+        total = sum(2 * ns for _, _, ns in self.shapes)
+        buf = np.zeros(total, dtype=np.float64)
+        self._check(lib().hqmc_logw_error(self._ctx, _ptr(buf)))
+        out, o = [], 0
+        for _, _, ns in self.shapes:
+            out.append(buf[o:o + 2 * ns].reshape(2, ns))
+            o += 2 * ns
+        return out
+
     def local_sweep(self, n=1):
         """Run n local-update sweeps (single-slice Metropolis moves of every worldline,
         then the Gibbs step and observables)."""
@@ -340,10 +365,29 @@ class Lattice:
             res.append(dict(n_samples=ob.n_samples, density=ob.density, double_occ=ob.double_occ, m2=ob.m2,
                             ekin=ob.ekin, s_pipi=ob.s_pipi, n_degenerate=ob.n_degenerate,
                             n_nonpositive=ob.n_nonpositive, n_local_accepted=ob.n_local_accepted,
-                            mean_sign=ob.mean_sign, n_perm_accepted=ob.n_perm_accepted,
+                            mean_sign=ob.mean_sign, n_perm_accepted=ob.n_perm_accepted, n_inexact=ob.n_inexact,
                             Sk=sk[o:o + N].copy(), Cr=cr[o:o + N].copy()))
             o += N
         return res
+
+    def set_measure_open(self, on=True):
+        """Accumulate the open-path estimator of the one-body density matrix (for n_k) in
+        every later sweep; restarts the observable accumulators."""
+        self._check(lib().hqmc_set_measure_open(self._ctx, int(bool(on))))
+
+    def measure_open(self):
+        """Per chain (n_k [N], one-body density matrix per site [N]) from the open-path sums
+        since the last reset (hqmc_measure_open)."""
+        self.prepare()
+        totN = sum(L * L for L, _, _ in self.shapes)
+        nk = np.zeros(totN)
+        dm = np.zeros(totN)
+        self._check(lib().hqmc_measure_open(self._ctx, _ptr(nk), _ptr(dm)))
+        out, o = [], 0
+        for L, _, _ in self.shapes:
+            out.append((nk[o:o + L * L].copy(), dm[o:o + L * L].copy()))
+            o += L * L
+        return out
 
     def get_state(self, chain):
         self.prepare()

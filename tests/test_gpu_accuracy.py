@@ -8,9 +8,12 @@ error, so autocorrelation within a chain does not bias it.  Sides that run the s
 Markov kernel from the same start share the law of every sweep, so they agree whether or
 not the burn-in reached equilibrium; different kernels are compared after a long one.  For every observable and
 every pair of sides the test forms z = (a - b) / sqrt(se_a^2 + se_b^2).  Under a correct
-sampler each z is a standard normal draw: the test asserts |z| < 4.5 for all of them and
-that the FP32 and FP64 standard errors agree within 20% (equal accuracy per sweep).  Run
-with `-s` to print the table of means, standard errors and z values.
+sampler each z is a standard normal draw: the test asserts |z| < 4.5 for all of them (a
+gross-bias guard), that no more of them exceed 2 than a binomial count with
+P(|z| > 2) = 0.0455 allows at the 99.9% level (the 2-sigma criterion: a bias of a few
+sigma in any observable pushes its z values past 2), and that the FP32 and FP64 standard
+errors agree within 20% (equal accuracy per sweep).  Run with `-s` to print the table of
+means, standard errors and z values.
 
 The particle density is conserved by every move, so it must equal the filling exactly.
 """
@@ -22,6 +25,25 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 NAMES = ("double_occ", "m2", "ekin", "s_pipi", "c_10")
+P2 = 0.0455  # P(|z| > 2) for a standard normal z
+
+
+def two_sigma_limit(n, alpha=1e-3):
+    """Largest count of |z| > 2 among n standard normal z values that a binomial law
+    (n, P2) exceeds with probability below alpha."""
+    from scipy.stats import binom
+
+    k = 0
+    while binom.sf(k, n, P2) >= alpha:
+        k += 1
+    return k
+
+
+def check_two_sigma(zs):
+    zs = np.abs(np.asarray(zs, dtype=float))
+    n2, lim = int((zs > 2.0).sum()), two_sigma_limit(len(zs))
+    print(f"|z| > 2: {n2} of {len(zs)} (binomial 99.9% limit {lim})")
+    assert n2 <= lim, (n2, lim, sorted(zs)[-5:])
 
 
 def gpu_side(L, params, prec, seeds, burn, meas, block=0, local=False, perm=False, signed=False):
@@ -108,16 +130,19 @@ def test_fp32_fp64_and_oracle_agree_statistically(L, params, n_gpu, n_orc, burn,
     print(f"{'observable':>11} | {'fp32 mean':>12} {'se':>9} | {'fp64 mean':>12} {'se':>9} | "
           f"{'oracle mean':>12} {'se':>9} | z32-64  z32-orc  z64-orc")
     worst = 0.0
+    allz = []
     for j, name in enumerate(NAMES):
         m32, m64, mor = (sides[k][0][j] for k in ("fp32", "fp64", "oracle"))
         s32, s64, sor = (sides[k][1][j] for k in ("fp32", "fp64", "oracle"))
         z = [(m32 - m64) / np.hypot(s32, s64), (m32 - mor) / np.hypot(s32, sor), (m64 - mor) / np.hypot(s64, sor)]
+        allz += z
         worst = max(worst, *map(abs, z))
         print(f"{name:>11} | {m32:12.6f} {s32:9.2e} | {m64:12.6f} {s64:9.2e} | {mor:12.6f} {sor:9.2e} | "
               + "  ".join(f"{v:+6.2f}" for v in z))
         assert all(abs(v) < 4.5 for v in z), (name, z)
         assert 0.8 < s32 / s64 < 1.25, (name, s32, s64)
     print(f"largest |z| = {worst:.2f}")
+    check_two_sigma(allz)
 
 
 def table(title, sides, names, ref=None):
@@ -130,13 +155,16 @@ def table(title, sides, names, ref=None):
     print(f"{'observable':>11} | " + " | ".join(f"{k:>10} mean {'se':>9}" for k in keys) + " | "
           + "  ".join(f"z {a}-{b}" for a, b in pairs))
     worst = 0.0
+    allz = []
     for j, name in enumerate(names):
         z = [(sides[a][0][j] - sides[b][0][j]) / np.hypot(sides[a][1][j], sides[b][1][j]) for a, b in pairs]
+        allz += z
         worst = max(worst, *map(abs, z))
         print(f"{name:>11} | " + " | ".join(f"{sides[k][0][j]:15.6f} {sides[k][1][j]:9.2e}" for k in keys)
               + " | " + "  ".join(f"{v:+6.2f}" for v in z))
         assert all(abs(v) < 4.5 for v in z), (name, z)
     print(f"largest |z| = {worst:.2f}")
+    check_two_sigma(allz)
     return worst
 
 

@@ -86,17 +86,18 @@ def test_fp64_attractive_tracks_the_oracle():
     lat.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("L,nwl", [(48, 6), (64, 4)])
-def test_wide_attractive_parity(L, nwl):
+def test_wide_attractive_parity(L, nwl, prec):
     params = (1.0, -4.0, 0.2, 0.05, 1.0)
-    lat = make(L, [12], "fp32", params)
+    lat = make(L, [12], prec, params)
     logw = lat.sweep(1, logw=True)
     orc = oracle.Chain(L, *params, 12)
     ref = orc.sweep(want_margin=True, nwl_limit=nwl)
     _, x, a, _ = lat.get_state(0)
     assert a == ref["anchor"]
-    assert rel_err(logw[0][:, :nwl], ref["logw"][:, :nwl]).max() <= 1e-5
-    _, _, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 1e-5, nwl=nwl)
+    assert rel_err(logw[0][:, :nwl], ref["logw"][:, :nwl]).max() <= TOL[prec]
+    _, _, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, TOL[prec], nwl=nwl)
     assert not bad, bad[:3]
     lat.close()
 

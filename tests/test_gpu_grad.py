@@ -172,3 +172,93 @@ def test_grad_l16_128_chains_sampled():
     assert np.abs(dvs[77] - rdv).max() <= 2.0 ** -6 * np.abs(rdv).max()
     assert abs(dt[77] - rdt) <= 2.0 ** -6 * abs(rdt)
     lat.close()
+
+
+# Measured on a GB300 (the shipped FP32 form with BF16 checkpoints every 9 slices, L = 16,
+# M = 80, half filling, 8 chains against the oracle): the largest marginal error relative to
+# the marginals' scale 1.08e-3, the largest relative d log Z / d t error 3.7e-5 (8.3e-6
+# against FP64 central differences), log Z 1.5e-7.  The bounds are about twice those.
+BF16_DV_BOUND = 2.5e-3
+BF16_DT_BOUND = 1e-4
+
+
+def test_grad_config4_bf16_accuracy_on_eight_chains():
+    """L=16, U=4, beta=4, dtau=0.05 (M=80), half filling, 128 chains, the default FP32 form
+    with BF16 checkpoints; eight chains against the oracle's forward-backward pass."""
+    params = (1.0, 4.0, 4.0, 0.05, 1.0)
+    lat = make(16, list(range(128)), "fp32", params, sweeps=3)
+    lz, dv, dt = lat.log_weight_grad()
+    dvs = split(lat, dv.double().cpu().numpy())
+    e_lz = e_dv = e_dt = 0.0
+    for c in (0, 17, 33, 50, 77, 90, 101, 127):
+        rz, rdv, rdt = oracle_grad(lat, c, params)
+        e_lz = max(e_lz, abs(lz[c] - rz) / max(1.0, abs(rz)))
+        e_dv = max(e_dv, np.abs(dvs[c] - rdv).max() / np.abs(rdv).max())
+        e_dt = max(e_dt, abs(dt[c] - rdt) / abs(rdt))
+    lat.close()
+    print(f"\nBF16 checkpoints, L=16 M=80, 8 chains: log Z {e_lz:.2e}, marginals {e_dv:.2e} of scale, "
+          f"d log Z/dt {e_dt:.2e} relative")
+    assert e_lz <= 1e-5
+    assert e_dv <= BF16_DV_BOUND
+    assert e_dt <= BF16_DT_BOUND
+
+
+def test_dt_fp32_bf16_against_fp64_finite_differences():
+    """The shipped FP32 + BF16 d log Z / d t at L = 16 (M = 80) against central differences
+    (h = 1e-6) of the GPU FP64 context's log Z on the same worldlines and fields."""
+    params = [1.0, 4.0, 4.0, 0.05, 1.0]
+    lat = make(16, [21, 22], "fp32", params, sweeps=3)
+    _, _, dt32 = lat.log_weight_grad()
+    states = [lat.get_state(c) for c in range(2)]
+    lat.close()
+    lat64 = make(16, [21, 22], "fp64", params, sweeps=0)
+    for c, (s, x, _, sw) in enumerate(states):
+        lat64.set_state(c, s, x, sweeps=sw)
+    h = 1e-6
+    lat64.set_params(1.0 + h, *params[1:])
+    zp = lat64.log_weight_grad()[0]
+    lat64.set_params(1.0 - h, *params[1:])
+    zm = lat64.log_weight_grad()[0]
+    lat64.close()
+    fd = (zp - zm) / (2 * h)
+    err = np.abs(dt32 - fd) / np.abs(fd)
+    print(f"\nFP32+BF16 d log Z/dt against FP64 central differences: {err.max():.2e} relative")
+    assert err.max() <= BF16_DT_BOUND, (dt32, fd)
+
+
+@pytest.mark.parametrize("prec,L,beta,dtau,fill,ckpt", [
+    ("fp32", 48, 0.35, 0.05, 14 / 2304, "full"),   # 7 worldlines per spin: a half-empty CTA
+    ("fp32", 64, 0.3, 0.05, 6 / 4096, "full"),
+    ("fp32", 128, 0.15, 0.05, 4 / 16384, "full"),
+    ("fp32", 64, 0.4, 0.05, 6 / 4096, "bf16"),
+    ("fp64", 48, 0.3, 0.05, 10 / 2304, "full"),
+    ("fp64", 64, 0.2, 0.05, 4 / 4096, "full"),
+])
+def test_wide_grad_matches_oracle(prec, L, beta, dtau, fill, ckpt):
+    """The wide-lattice adjoint (one thread per line of each worldline; d log Z / d t from
+    dG/dt = dtau A G) against the oracle's forward-backward pass: log Z, the marginals and
+    d log Z / d t."""
+    params = (1.0, 4.0, beta, dtau, fill)
+    lat = make(L, [3], prec, params)
+    lat.set_checkpoint(2, bf16=(ckpt == "bf16"))
+    if prec == "fp64":
+        tol = (1e-10, 1e-10)
+    else:
+        tol = (1e-5, 1e-4 if ckpt == "full" else BF16_DV_BOUND)
+    check(lat, params, *tol, chains=[0])
+    lat.close()
+
+
+def test_wide_dt_against_gpu_finite_differences():
+    """FP64 context at L = 48: d log Z / d t against central differences of its own log Z."""
+    params = [1.0, 4.0, 0.4, 0.05, 10 / 2304]
+    lat = make(48, [4], "fp64", params)
+    _, _, dt = lat.log_weight_grad()
+    h = 1e-6
+    lat.set_params(1.0 + h, *params[1:])
+    zp = lat.log_weight_grad()[0][0]
+    lat.set_params(1.0 - h, *params[1:])
+    zm = lat.log_weight_grad()[0][0]
+    fd = (zp - zm) / (2 * h)
+    assert abs(fd - dt[0]) <= 1e-6 * max(1.0, abs(dt[0])), (fd, dt[0])
+    lat.close()
