@@ -379,6 +379,9 @@ def main():
                          "(M=1024); grad16 times the adjoint")
     ap.add_argument("--local-steps", type=int, default=20,
                     help="local-update sweeps timed beside the FFBS sweep (0: skip)")
+    ap.add_argument("--fstore", default="stream", choices=["stream", "bf16", "f32"],
+                    help="storage of f for the wide kernel's backward pass: every slice in FP32 (stream), or "
+                         "checkpoints every ceil(sqrt M) slices in BF16 / FP32 with the segments recomputed")
     ap.add_argument("--conv", default="fft", choices=["fft", "stencil"],
                     help="line convolutions of the FFBS filter (stencil: the truncated-stencil comparison)")
     ap.add_argument("--perm", action="store_true",
@@ -443,6 +446,8 @@ def main():
             lt.set_permutations(True)
         if args.conv != "fft":
             lt.set_conv(args.conv)
+        if args.fstore != "stream" and precision == "fp32":
+            lt.set_ffbs_storage(args.fstore)
         lt.prepare()
         return lt
 
@@ -483,6 +488,16 @@ def main():
     part_slices = sum(2 * ns * M for (_, M, ns) in shapes)
     alg_bytes = sum(2 * ns * M * 8.0 * L * L for (L, M, ns) in shapes)
     alg_flops = sum(2 * ns * M * (5.0 * L * L * np.log2(L * L) + 4.0 * L * L) for (L, M, ns) in shapes)
+    ckpt_note = None
+    if args.fstore != "stream" and max(Ls) > 32:
+        # checkpoints every K = ceil(sqrt M) slices: f written and read back once per K slices
+        # (2 bytes per site in BF16, 4 in FP32), and the filter run twice (forward, recompute);
+        # the recomputed segment goes through a per-CTA buffer (written and read, FP32)
+        cb = 2.0 if args.fstore == "bf16" else 4.0
+        alg_bytes = sum(2 * ns * L * L * (2 * cb * np.ceil(M / np.ceil(np.sqrt(M))) + 8.0 * M) for (L, M, ns) in shapes)
+        alg_flops *= 2.0
+        ckpt_note = ("f kept every ceil(sqrt M) slices (" + args.fstore + "); bytes = checkpoints written and read + "
+                     "the recomputed segments through the per-CTA buffer; flops = forward + recompute")
     hbm_peak, peak_src, sm_max = peaks()
     achieved = alg_bytes / (ffbs_avg / 1e3) / 1e9
     peak_alu, alu_src = alu_peak(local)
@@ -500,12 +515,21 @@ def main():
         except Exception:
             traffic = None
     kname = "ffbs_kernel<float,32>" if args.workload == "L32" else "FFBS launches (all sizes)"
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+    roofline = {"bound": "hbm" if ckpt_note is None else "alu", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
                 "peak_source": peak_src, "kernel": kname, "kernel_ms": ffbs_avg, "gibbs_measure_ms": slice_avg,
                 "alg_bytes_per_launch": alg_bytes,
                 "alu": {"achieved_tflops": achieved_flops, "peak_tflops": peak_alu,
                         "frac": achieved_flops / peak_alu, "peak_source": alu_src}}
+    if ckpt_note is not None:
+        # the recompute makes the checkpoint form an FP32-ALU-bound filter: the ALU figures
+        # lead, the bytes stand beside them
+        roofline.update({"achieved": achieved_flops, "peak": peak_alu, "unit": "TFLOP/s",
+                         "frac": achieved_flops / peak_alu, "peak_source": alu_src, "traffic": None,
+                         "traffic_note": "no DRAM counters for the checkpoint form",
+                         "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                                 "peak_source": peak_src},
+                         "storage": ckpt_note})
     # the Gibbs/measure kernel: per site-slice two int32 counts read and cleared (16 B)
     # and the field bits written twice (2 x 1 bit); the counts were just written by the
     # FFBS atomics and sit in L2, so HBM is not what bounds it
@@ -619,6 +643,8 @@ def main():
             wl += "; permutation updates at tau = beta"
         if args.conv != "fft":
             wl += "; line convolutions by the periodic stencil (|d| <= 6)"
+        if args.fstore != "stream" and max(Ls) > 32:
+            wl += f"; f checkpoints every ceil(sqrt M) slices in {args.fstore.upper()}, segments recomputed"
         if args.workload == "L32" and args.beta:
             wl += f"; beta={args.beta:g} instead (M={shapes[0][1]})"
         line = {"metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,

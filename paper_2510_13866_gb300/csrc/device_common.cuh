@@ -33,12 +33,19 @@ using vec2_t = typename vec2_of<T>::type;
 __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// the pair is assembled from and split into its two f32 halves inside the asm, so no
+// value is reinterpreted through a pointer of another type (which would break when the
+// compiler keeps the pair in local memory)
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) {
-    unsigned long long r;
-    const unsigned long long x = *reinterpret_cast<const unsigned long long *>(&a);
-    const unsigned long long y = *reinterpret_cast<const unsigned long long *>(&b);
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
-    return *reinterpret_cast<float2 *>(&r);
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
 __device__ __forceinline__ float2 vsplat(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }

@@ -92,8 +92,12 @@ __device__ __forceinline__ void store_ckpt(const float (&v)[L], float *slot, int
             const __nv_bfloat162 b = __floats2bfloat162_rn(v[8 * j + 2], v[8 * j + 3]);
             const __nv_bfloat162 c = __floats2bfloat162_rn(v[8 * j + 4], v[8 * j + 5]);
             const __nv_bfloat162 d = __floats2bfloat162_rn(v[8 * j + 6], v[8 * j + 7]);
-            dst[j * L + p] = make_uint4(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b),
-                                        *reinterpret_cast<const unsigned *>(&c), *reinterpret_cast<const unsigned *>(&d));
+            unsigned ua, ub, uc, ud;
+            memcpy(&ua, &a, 4);
+            memcpy(&ub, &b, 4);
+            memcpy(&uc, &c, 4);
+            memcpy(&ud, &d, 4);
+            dst[j * L + p] = make_uint4(ua, ub, uc, ud);
         });
     } else {
         float4 *dst = reinterpret_cast<float4 *>(slot + (long long)s * N);
@@ -111,10 +115,15 @@ __device__ __forceinline__ void load_ckpt(float (&v)[L], const float *slot, int 
         static_for<0, L / 8>([&](auto JI) {
             constexpr int j = decltype(JI)::value;
             const uint4 q = src[j * L + p];
-            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
-            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
-            const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.z));
-            const float2 d = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.w));
+            __nv_bfloat162 ba, bb, bc, bd;
+            memcpy(&ba, &q.x, 4);
+            memcpy(&bb, &q.y, 4);
+            memcpy(&bc, &q.z, 4);
+            memcpy(&bd, &q.w, 4);
+            const float2 a = __bfloat1622float2(ba);
+            const float2 b = __bfloat1622float2(bb);
+            const float2 c = __bfloat1622float2(bc);
+            const float2 d = __bfloat1622float2(bd);
             unpack16<8 * j>(v, make_float4(a.x, a.y, b.x, b.y));
             unpack16<8 * j + 4>(v, make_float4(c.x, c.y, d.x, d.y));
         });

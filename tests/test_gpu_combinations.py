@@ -63,6 +63,10 @@ def draw_cases(n=48, seed=2510):
 
 CASES = draw_cases()
 
+# |log-weight error| / the library's estimate, per precision and convolution, gathered by the
+# random combinations and summarised by the last test of this file
+RATIOS = {}
+
 
 def slice_potentials(orc):
     """W [2][M][N] of the oracle chain's current fields (Hirsch: exp(+-lambda s) by spin;
@@ -151,10 +155,13 @@ def test_random_combination_matches_oracle(case):
             assert sw == k + 1 and a == ref["anchor"], (k, c)
             err = rel_err(logw[c], ref["logw"])
             flagged = ~(lerr[c] <= tol * np.maximum(1.0, np.abs(logw[c])))
+            ok = np.isfinite(lerr[c]) & np.isfinite(ref["logw"]) & (lerr[c] > 0)
+            RATIOS.setdefault((prec, stencil, params[1] < 0), []).extend(
+                (np.abs(logw[c] - ref["logw"])[ok] / lerr[c][ok]).tolist())
             assert nflag[c] == int(flagged.sum()), (k, c, nflag[c], int(flagged.sum()))
             strong64 = prec == "fp64" and params[1] < 0 and abs(params[1]) * params[3] >= 0.4
             for sg, p in zip(*np.nonzero(err > tol)):
-                if strong64 and not flagged[sg, p]:
+                if strong64:
                     assert err[sg, p] <= 2e-11, (k, c, sg, p, err[sg, p])  # the documented floor
                     continue
                 # beyond the plain tolerance only where the library flags the log-weight, and
@@ -247,3 +254,21 @@ def test_autotune_keeps_results_with_every_option():
         assert np.array_equal(perm, perm0) and sign == sign0, c
     assert np.array_equal(lat.get_sigma(1), sig_ref)
     lat.close()
+
+
+def test_zz_error_estimate_calibration():
+    """Distribution of |log-weight error| / estimate over the random combinations above (run
+    with -s to print it).  The FP32 FFT filter's errors stay within their estimate: the
+    estimate eps log2(N) len kappa uses the end concentration for every slice, and in FP32
+    the rounding at the end dominates.  FP64 is printed, not bounded: strong Gaussian fields
+    concentrate the message more at interior slices than at the end."""
+    if not RATIOS:
+        pytest.skip("the random combinations did not run in this session")
+    print()
+    for (prec, stencil, gauss), r in sorted(RATIOS.items()):
+        r = np.asarray(r)
+        print(f"{prec} {'stencil' if stencil else 'fft':>7} {'U<0' if gauss else 'U>=0':>4}: {len(r):5d} log-weights, "
+              f"error / estimate: median {np.median(r):.3g}, 99th percentile {np.percentile(r, 99):.3g}, "
+              f"max {r.max():.3g}")
+    fp32_fft = np.concatenate([np.asarray(r) for (prec, st, _), r in RATIOS.items() if prec == "fp32" and not st])
+    assert fp32_fft.max() <= 1.0, fp32_fft.max()
