@@ -134,12 +134,15 @@ __device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_
     else cp_async8(sdst + sc, gsrc + gc);
 }
 
+// GAUSS: the class holds Gaussian-field chains (U < 0): their slice potentials are read from
+// the W arrays and their log-weight estimate tracks the interior concentration; the Hirsch-
+// only instantiation carries none of that code.
 // STN: line convolutions by the periodic stencil (stencil_store) instead of the FFT.
 // BLK: the general work units -- FFBS blocks B < M and/or a permutation at tau = beta (the
 // closed-loop instantiation carries none of that bookkeeping).  With a permutation P the
 // unit of worldline p runs from slice a of p to slice a of P(p): its positions at or past
 // the wrap (a + offset >= M) are slices of worldline P(p).
-template <typename T, int L, bool BLK, bool STN>
+template <typename T, int L, bool BLK, bool STN, bool GAUSS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevState st, FfbsLaunch fl) {
     using G = FfbsGeo<T, L>;
     using V = vec2_t<T>;
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             const int sx0 = xs0 % L, sy0 = xs0 / L, sx1 = xs1 % L, sy1 = xs1 / L;
             // f_{l0} = W_{l0}(x_{l0}) delta_{x_{l0}}, layout R: lane = iy, register = ix
             T wv0, wv1;
-            if (cd.gauss) {
+            if (GAUSS && cd.gauss) {
                 wv0 = gauss_line<T>(st, cd, false, l0, sy0)[sx0];
                 wv1 = gauss_line<T>(st, cd, false, l0, sy1)[sx1];
             } else {
@@ -283,12 +286,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         int esum0 = 0, esum1 = 0;
         T fin0 = T(0), fin1 = T(0);
         T top0 = T(0), top1 = T(0);  // largest value of the final message (kappa = top / fin)
+        // Gaussian-field units: sum over interior positions of max alpha / alpha at the
+        // worldline's current site there (strong fields concentrate the message inside the
+        // block more than at its end; Hirsch units use the end value alone)
+        float ksum0 = 0.f, ksum1 = 0.f;
         int l = l0;
         for (int i = 0; i < len; ++i) {
             // the next slice's field bits (Hirsch chains), loaded before this slice's
             // convolutions so that their latency is hidden behind them
             uint32_t wnext = 0u;
-            if (!cd.gauss && active && i < len - 1) {
+            if (!(GAUSS && cd.gauss) && active && i < len - 1) {
                 const int ln1 = (l + 1 == M) ? 0 : l + 1;
                 wnext = ((i & 1) ? srow : scol)[((long long)ln1 * L + gl) * cd.wpl];
             }
@@ -382,7 +389,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 const T sc0 = fbits<T>::pow2(-e0), sc1 = fbits<T>::pow2(-e1);
                 const V A = {wp * sc0, wp * sc1}, B = {wm * sc0, wm * sc1};
                 // the new layout is C (lane = ix) when i is even: the field by columns
-                if (cd.gauss) {
+                if (GAUSS && cd.gauss) {
+                    {
+                        // v = alpha of position i + 1 (layout C if i + 1 is odd)
+                        const bool oc = (i & 1) == 0;
+                        const int xo0 = owner0(i + 1)[l1];
+                        const int xo1 = has1 ? int(owner1(i + 1)[l1]) : xo0;
+                        const int own0 = oc ? xo0 % L : xo0 / L, reg0 = oc ? xo0 / L : xo0 % L;
+                        const int own1 = oc ? xo1 % L : xo1 / L, reg1 = oc ? xo1 / L : xo1 % L;
+                        V mx = vzero(v[0]);
+#pragma unroll
+                        for (int r = 0; r < L; ++r) {
+                            mx.x = v[r].x > mx.x ? v[r].x : mx.x;
+                            mx.y = v[r].y > mx.y ? v[r].y : mx.y;
+                        }
+                        const T m0 = group_max<GW>(mx.x, gmask), m1 = group_max<GW>(mx.y, gmask);
+                        const T a0 = __shfl_sync(gmask, reg_select<L>(v, reg0).x, own0, GW);
+                        const T a1 = __shfl_sync(gmask, reg_select<L>(v, reg1).y, own1, GW);
+                        const float inf = __int_as_float(0x7f800000);
+                        ksum0 += a0 > T(0) ? float(m0 / a0) : inf;
+                        ksum1 += a1 > T(0) ? float(m1 / a1) : inf;
+                    }
                     if (active) mul_gauss_line<T, L>(v, gauss_line<T>(st, cd, (i & 1) == 0, l1, gl), sc0, sc1);
                 } else {
                     const uint32_t w = wnext;
@@ -438,8 +465,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             const double inf = __longlong_as_double(0x7ff0000000000000LL);
-            const double err0 = fin0 > T(0) ? logw_err_estimate<T>(double(top0) / double(fin0), len, L, STN) : inf;
-            const double err1 = fin1 > T(0) ? logw_err_estimate<T>(double(top1) / double(fin1), len, L, STN) : inf;
+            // Hirsch units: len x the end concentration; Gaussian units: the interior
+            // concentrations summed, plus the end's
+            const double kap0 = double(top0) / double(fin0), kap1 = double(top1) / double(fin1);
+            const double err0 = !(fin0 > T(0)) ? inf
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(ksum0) + kap0) / len, len, L, STN)
+                                           : logw_err_estimate<T>(kap0, len, L, STN);
+            const double err1 = !(fin1 > T(0)) ? inf
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(ksum1) + kap1) / len, len, L, STN)
+                                           : logw_err_estimate<T>(kap1, len, L, STN);
             // a log-weight whose estimate exceeds the tolerance is counted (hqmc_obs.n_inexact)
             auto flag = [&](double lwv, double e) {
                 if (!(e <= logw_tolerance<T>() * fmax(1.0, fabs(lwv)))) atomicAdd(&st.meas[c].inexact, 1ull);

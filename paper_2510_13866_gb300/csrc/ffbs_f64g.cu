@@ -1,0 +1,10 @@
+// ffbs_f64g.cu -- FP64 instantiations of the FFBS kernel for classes with Gaussian-field
+// (U < 0) chains.
+#include "ffbs_launch.cuh"
+
+namespace hqmc {
+cudaError_t launch_ffbs_f64g(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s) {
+    return ffbs_dispatch<double, true>(L, st, fl, grid, wpc, s);
+}
+cudaError_t ffbs_occupancy_f64g(int L, int wpc, int *blocks) { return ffbs_occ_dispatch<double, true>(L, wpc, blocks); }
+}  // namespace hqmc

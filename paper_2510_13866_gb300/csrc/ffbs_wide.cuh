@@ -338,6 +338,9 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             return e;
         };
         const int K = CKPT ? fl.ckpt_K : 0;  // 0: every f streamed; else f kept every K positions
+        // Gaussian-field units: sum over interior positions of max alpha / alpha at the
+        // worldline's current site there (see the log-weight estimate below)
+        T ksum = T(0);
         for (int i = 0; i < len; ++i) {
             if (has) {
                 if (K == 0) {
@@ -348,6 +351,23 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             }
             const T s = conv_sum();
             if (i < len - 1) {
+                if (cd.gauss) {
+                    // v = alpha of position i + 1 (layout C if i + 1 is odd)
+                    const bool oc = (i & 1) == 0;
+                    const int xo = owner(i + 1)[slice_of(i + 1)];
+                    const int own = oc ? xo % L : xo / L, reg = oc ? xo / L : xo % L;
+                    T mx = T(0);
+#pragma unroll
+                    for (int r = 0; r < L; ++r) mx = v[r] > mx ? v[r] : mx;
+                    mx = wl_warp_max<WPC>(mx);
+                    if (lane < WPC) wmx[warp * WPC + lane] = mx;
+                    if (p == own) endv[2 * WPC + w] = reg_select<L>(v, reg);
+                    __syncthreads();
+                    T top = wmx[w];
+                    for (int k = 1; k < NW; ++k) top = wmx[k * WPC + w] > top ? wmx[k * WPC + w] : top;
+                    const T a = endv[2 * WPC + w];
+                    ksum += a > T(0) ? top / a : T(__int_as_float(0x7f800000));
+                }
                 esum += renorm_w(i, s, true);
             } else {
                 // alpha_{l0+len}(x_{l0+len}): the final layout is C if len is odd; its
@@ -382,7 +402,10 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                     for (int k = 1; k < NW; ++k) top = wmx[k * WPC + tid] > top ? wmx[k * WPC + tid] : top;
                     endv[WPC + tid] = top;
                 }
-                if (p == 0) ibuf[9 + w] = esum;
+                if (p == 0) {
+                    ibuf[9 + w] = esum;
+                    endv[3 * WPC + w] = ksum;
+                }
                 __syncthreads();
             }
         }
@@ -395,7 +418,12 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             for (int k = 0; k < nwl; ++k) {
                 const T fin = endv[k], top = endv[WPC + k];
                 part[k] = double(ibuf[9 + k]) * ln2 + log(double(fin));
-                err[k] = fin > T(0) ? logw_err_estimate<T>(double(top) / double(fin), len, L, false) : inf;
+                // Hirsch units: len x the end concentration; Gaussian units: the interior
+                // concentrations summed, plus the end's
+                const double kap = double(top) / double(fin);
+                err[k] = !(fin > T(0)) ? inf
+                         : cd.gauss ? logw_err_estimate<T>((double(endv[3 * WPC + k]) + kap) / len, len, L, false)
+                                    : logw_err_estimate<T>(kap, len, L, false);
                 if (!(fin > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             }
             auto flag = [&](double lwv, double e) {

@@ -132,6 +132,7 @@ struct FfbsLaunch {
     int ckpt_K;
     int ckpt_bf16;
     long long seg_off;
+    int gauss;                 // some chain of the class has a Gaussian field (U < 0)
 };
 
 // One launch of the adjoint kernel covers the chains of one lattice size.

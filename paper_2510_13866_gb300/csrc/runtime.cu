@@ -15,6 +15,10 @@ cudaError_t launch_ffbs_f32(int L, const DevState &st, const FfbsLaunch &fl, int
 cudaError_t launch_ffbs_f64(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s);
 cudaError_t ffbs_occupancy_f32(int L, int wpc, int *blocks);
 cudaError_t ffbs_occupancy_f64(int L, int wpc, int *blocks);
+cudaError_t launch_ffbs_f32g(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s);
+cudaError_t launch_ffbs_f64g(int L, const DevState &st, const FfbsLaunch &fl, int grid, int wpc, cudaStream_t s);
+cudaError_t ffbs_occupancy_f32g(int L, int wpc, int *blocks);
+cudaError_t ffbs_occupancy_f64g(int L, int wpc, int *blocks);
 size_t ffbs_smem_f32(int L, int wpc);
 size_t ffbs_smem_f64(int L, int wpc);
 cudaError_t launch_grad_f32(int L, const DevState &st, const GradLaunch &gk, int grid, cudaStream_t s);
@@ -295,6 +299,13 @@ int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
     cudaError_t e = is_big(L) ? ffbs_wide_occupancy(L, c->precision == HQMC_FP64, blocks)
                     : c->precision == HQMC_FP64 ? ffbs_occupancy_f64(L, wpc, blocks)
                                                 : ffbs_occupancy_f32(L, wpc, blocks);
+    if (e == cudaSuccess && !is_big(L)) {
+        // the Gaussian-field instantiations get their limits too; the grid follows the
+        // smaller residency of the two
+        int bg = 0;
+        e = c->precision == HQMC_FP64 ? ffbs_occupancy_f64g(L, wpc, &bg) : ffbs_occupancy_f32g(L, wpc, &bg);
+        if (e == cudaSuccess && bg > 0) *blocks = std::min(*blocks, bg);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (*blocks < 1) *blocks = 1;
     return HQMC_OK;
@@ -694,9 +705,13 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
         HQMC_CUDA(c, cudaMemsetAsync(fl.next_unit, 0, sizeof(unsigned), s));
         const int wpc = default_wpc(c, cl.L);
+        fl.gauss = 0;
+        for (int ci : cl.chains) fl.gauss |= c->cdev[ci].gauss;
         cudaError_t e = is_big(cl.L) ? launch_ffbs_wide(cl.L, f64, c->st, fl, cl.grid, s)
-                        : f64        ? launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s)
-                                     : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s);
+                        : f64 ? (fl.gauss ? launch_ffbs_f64g(cl.L, c->st, fl, cl.grid, wpc, s)
+                                          : launch_ffbs_f64(cl.L, c->st, fl, cl.grid, wpc, s))
+                              : (fl.gauss ? launch_ffbs_f32g(cl.L, c->st, fl, cl.grid, wpc, s)
+                                          : launch_ffbs_f32(cl.L, c->st, fl, cl.grid, wpc, s));
         if (e != cudaSuccess) return cuda_fail(c, e, "ffbs launch");
     }
     if (nk > 1) {
