@@ -219,16 +219,18 @@ int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
  * of a slice with a rounding error of about eps log2(N) of the slice's largest value, so a
  * site that ends kappa = max_y alpha_end(y) / alpha_end(x_end) times below the largest
  * carries about eps log2(N) kappa from each slice.  The estimate of a block of len slices
- * is eps log2(N) len kappa (eps = 2^-24 in FP32, 2^-53 in FP64; the end concentration
- * stands in for every slice's), summed over the worldline's blocks; with
- * HQMC_CONV_STENCIL every output is a sum of non-negative terms that keeps its own
- * relative accuracy and kappa is replaced by 1.  A non-positive end value gives +inf.
- * Worldlines whose estimate exceeds the precision's tolerance are counted in
- * hqmc_obs.n_inexact; where this matters (strong fields concentrate the message, kappa of
- * 1e4 and beyond) the stencil form gives the accurate value.  Calibration against a direct
- * O(N^2) convolution: FP32 errors stayed below 0.73 of the estimate; FP64 errors under
- * strong Gaussian fields (U < 0 with |U| dtau >= 0.4, where the message concentrates more
- * at interior slices than at the end) reached 1.3e-11 relative without a flag.
+ * is eps log2(N) len kappa for a Hirsch field (eps = 2^-24 in FP32, 2^-53 in FP64; the end
+ * concentration stands in for every slice's) and eps log2(N) sum_i max_y alpha_i(y) /
+ * alpha_i(x_i) for a Gaussian field, over the block's positions i at the sites x_i the
+ * sweep drew (a strong Gaussian field concentrates the message more inside the block than
+ * at its end; over the drawn path this sum has the mean that propagates slice i's rounding
+ * to the log-weight), summed over the worldline's blocks.  With HQMC_CONV_STENCIL every
+ * output is a sum of non-negative terms that keeps its own relative accuracy and kappa is
+ * replaced by 1.  A non-positive end value gives +inf.  Worldlines whose estimate exceeds
+ * the precision's tolerance are counted in hqmc_obs.n_inexact; where this matters (strong
+ * fields concentrate the message, kappa of 1e4 and beyond) the stencil form gives the
+ * accurate value.  The estimate is calibrated, not a bound: against a direct O(N^2)
+ * convolution, FP32 errors stayed below 0.73 of it.
  * Errors: HQMC_ERR_ARG, HQMC_ERR_STATE (no sweep yet), HQMC_ERR_CUDA. */
 int hqmc_logw_error(hqmc_ctx *ctx, double *err_out);
 

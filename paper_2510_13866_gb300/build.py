@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libhqmc.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["runtime.cu", "slice.cu", "ffbs_f32.cu", "ffbs_f64.cu", "ffbs_f32g.cu", "ffbs_f64g.cu", "grad_f32.cu", "grad_f64.cu", "ffbs_wide.cu", "grad_wide.cu", "noalloc.cu", "local.cu", "peak.cu"]
+SOURCES = ["runtime.cu", "slice.cu", "ffbs_f32.cu", "ffbs_f64.cu", "ffbs_f32g.cu", "ffbs_f64g.cu", "grad_f32.cu", "grad_f64.cu", "ffbs_wide.cu", "ffbs_wide_g.cu", "grad_wide.cu", "noalloc.cu", "local.cu", "peak.cu"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
 

@@ -286,10 +286,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         int esum0 = 0, esum1 = 0;
         T fin0 = T(0), fin1 = T(0);
         T top0 = T(0), top1 = T(0);  // largest value of the final message (kappa = top / fin)
-        // Gaussian-field units: sum over interior positions of max alpha / alpha at the
-        // worldline's current site there (strong fields concentrate the message inside the
-        // block more than at its end; Hirsch units use the end value alone)
-        float ksum0 = 0.f, ksum1 = 0.f;
+        // Gaussian-field units keep max_y alpha_i(y) of every interior position i (at the
+        // scale of the stored f_i) after the unit's f slices, for the backward pass
+        V *aux = slot + (long long)fl.len_max * N;
         int l = l0;
         for (int i = 0; i < len; ++i) {
             // the next slice's field bits (Hirsch chains), loaded before this slice's
@@ -391,12 +390,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                 // the new layout is C (lane = ix) when i is even: the field by columns
                 if (GAUSS && cd.gauss) {
                     {
-                        // v = alpha of position i + 1 (layout C if i + 1 is odd)
-                        const bool oc = (i & 1) == 0;
-                        const int xo0 = owner0(i + 1)[l1];
-                        const int xo1 = has1 ? int(owner1(i + 1)[l1]) : xo0;
-                        const int own0 = oc ? xo0 % L : xo0 / L, reg0 = oc ? xo0 / L : xo0 % L;
-                        const int own1 = oc ? xo1 % L : xo1 / L, reg1 = oc ? xo1 / L : xo1 % L;
+                        // v = alpha of position i + 1
                         V mx = vzero(v[0]);
 #pragma unroll
                         for (int r = 0; r < L; ++r) {
@@ -404,11 +398,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                             mx.y = v[r].y > mx.y ? v[r].y : mx.y;
                         }
                         const T m0 = group_max<GW>(mx.x, gmask), m1 = group_max<GW>(mx.y, gmask);
-                        const T a0 = __shfl_sync(gmask, reg_select<L>(v, reg0).x, own0, GW);
-                        const T a1 = __shfl_sync(gmask, reg_select<L>(v, reg1).y, own1, GW);
-                        const float inf = __int_as_float(0x7f800000);
-                        ksum0 += a0 > T(0) ? float(m0 / a0) : inf;
-                        ksum1 += a1 > T(0) ? float(m1 / a1) : inf;
+                        if (gl == 0) aux[i + 1] = V{m0 * sc0, m1 * sc1};
                     }
                     if (active) mul_gauss_line<T, L>(v, gauss_line<T>(st, cd, (i & 1) == 0, l1, gl), sc0, sc1);
                 } else {
@@ -456,7 +446,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             }
             l = l1;
         }
-        if (gl == 0) {
+        // the unit's log-weights and their error estimates; Hirsch units book them after the
+        // forward pass, Gaussian-field units after the backward pass, which supplies kin
+        auto book = [&](double kin0, double kin1) {
+            if (gl != 0) return;
             // log-weight of the block; with several blocks, the pair's last finished block
             // sums the partials in block order (the same bits whichever finishes last)
             const double ln2 = 0.69314718055994530942;
@@ -465,14 +458,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             const double inf = __longlong_as_double(0x7ff0000000000000LL);
-            // Hirsch units: len x the end concentration; Gaussian units: the interior
-            // concentrations summed, plus the end's
+            // Hirsch units: len x the end concentration; Gaussian units: the concentrations
+            // at the drawn sites of positions 1 .. len-1 (kin, from the backward pass), plus
+            // the end's
             const double kap0 = double(top0) / double(fin0), kap1 = double(top1) / double(fin1);
             const double err0 = !(fin0 > T(0)) ? inf
-                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(ksum0) + kap0) / len, len, L, STN)
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(kin0) + kap0) / len, len, L, STN)
                                            : logw_err_estimate<T>(kap0, len, L, STN);
             const double err1 = !(fin1 > T(0)) ? inf
-                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(ksum1) + kap1) / len, len, L, STN)
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(kin1) + kap1) / len, len, L, STN)
                                            : logw_err_estimate<T>(kap1, len, L, STN);
             // a log-weight whose estimate exceeds the tolerance is counted (hqmc_obs.n_inexact)
             auto flag = [&](double lwv, double e) {
@@ -523,7 +517,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                     *done = 0u;  // ready for the next sweep
                 }
             }
-        }
+        };
+        if (!(GAUSS && cd.gauss)) book(0.0, 0.0);
 
         // ---- backward sampling ----
         // slice i of the slot -> xbuf: R slices (i even) chunk-for-chunk, C slices (i odd)
@@ -554,6 +549,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         }
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
+        // Gaussian-field units: sum over positions i of max_y alpha_i(y) / alpha_i(x_i) at the
+        // drawn sites (alpha_i = f_i / W_i).  The draws follow the unit's posterior, under
+        // which the mean of this ratio is max alpha_i sum_y beta_i(y) / <alpha_i, beta_i>
+        // (beta_i the backward message from the held end): the factor by which a rounding
+        // error of the size of max alpha_i at slice i reaches the log-weight.  The three
+        // values of a draw are loaded at once and used one position later.
+        T kin0 = T(0), kin1 = T(0);
+        T pf0 = T(0), pf1 = T(0), pw0 = T(0), pw1 = T(0), pm0 = T(0), pm1 = T(0);
+        bool pend = false;
+        auto take = [&]() {
+            if (pend) {
+                const T inf = T(1) / T(0);
+                kin0 += pf0 > T(0) ? pm0 * pw0 / pf0 : inf;
+                kin1 += pf1 > T(0) ? pm1 * pw1 / pf1 : inf;
+            }
+        };
         for (int i = len - 1; i >= 1; --i) {
             int lb = l0 + i;
             if (lb >= M) lb -= M;
@@ -717,8 +728,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                     atomicAdd(hist_s + (long long)lb * N + nxt1, 1);
                 }
             }
+            if constexpr (GAUSS) {
+                if (cd.gauss && gl == 0) {
+                    take();
+                    // element x of position i in the writer's layout (R for even i: lane = iy,
+                    // register = ix; C for odd i)
+                    const bool ev = (i & 1) == 0;
+                    auto fat = [&](int x) {
+                        const int r = ev ? x % L : x / L, q = ev ? x / L : x % L;
+                        return slot + (long long)i * N + ((long long)(r / CH) * L + q) * CH + r % CH;
+                    };
+                    pf0 = __ldcg(&fat(nxt0)->x);
+                    pf1 = __ldcg(&fat(nxt1)->y);
+                    pw0 = gauss_line<T>(st, cd, false, lb, nxt0 / L)[nxt0 % L];
+                    pw1 = gauss_line<T>(st, cd, false, lb, nxt1 / L)[nxt1 % L];
+                    const V am = __ldcg(aux + i);
+                    pm0 = am.x;
+                    pm1 = am.y;
+                    pend = true;
+                }
+            }
             cur0 = nxt0;
             cur1 = nxt1;
+        }
+        if constexpr (GAUSS) {
+            if (cd.gauss) {
+                if (gl == 0) take();
+                book(double(kin0), double(kin1));
+            }
         }
         if (gl == 0) {
             // link x_{l0} -> x_{l0+1}

@@ -1,11 +1,12 @@
 // ffbs_wide.cu -- instantiations of the wide-lattice FFBS kernel (L = 48, 64, 128; FP32
-// and FP64) and its host-side geometry.
+// and FP64) for Hirsch-field classes, and the host-side geometry.
 #include "ffbs_launch.cuh"
 #include "ffbs_wide.cuh"
 
 namespace hqmc {
 
-#define HQMC_WIDE_SIZES(X) X(48) X(64) X(128)
+cudaError_t ffbs_wide_occupancy_g(int L, bool fp64, int *blocks);
+cudaError_t launch_ffbs_wide_g(int L, bool fp64, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s);
 
 bool ffbs_wide_supported(int L) {
     switch (L) {
@@ -28,44 +29,18 @@ int ffbs_wide_wpc(int L) {
     }
 }
 
-template <typename T, int L>
-static cudaError_t wide_occ(int *blocks) {
-    if constexpr (sizeof(T) == 4) {
-        cudaError_t e = raise_smem_limit(ffbs_wide_kernel<T, L, true>, WideGeo<T, L>::BYTES);
-        if (e != cudaSuccess) return e;
-    }
-    auto k = ffbs_wide_kernel<T, L, false>;
-    cudaError_t e = raise_smem_limit(k, WideGeo<T, L>::BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, WideGeo<T, L>::NT, WideGeo<T, L>::BYTES);
-}
-
+// both Gaussian flags get their limits; the grid follows the smaller residency
 cudaError_t ffbs_wide_occupancy(int L, bool fp64, int *blocks) {
-    switch (L) {
-#define HQMC_CASE(n) \
-    case n: return fp64 ? wide_occ<double, n>(blocks) : wide_occ<float, n>(blocks);
-        HQMC_WIDE_SIZES(HQMC_CASE)
-#undef HQMC_CASE
-        default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = wide_occ_dispatch<false>(L, fp64, blocks);
+    if (e != cudaSuccess) return e;
+    int bg = 0;
+    e = ffbs_wide_occupancy_g(L, fp64, &bg);
+    if (e == cudaSuccess && bg > 0 && bg < *blocks) *blocks = bg;
+    return e;
 }
 
-// launch only: the shared-memory limit is raised beforehand (never during stream capture)
 cudaError_t launch_ffbs_wide(int L, bool fp64, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s) {
-    switch (L) {
-#define HQMC_CASE(n)                                                                                        \
-    case n:                                                                                                 \
-        if (fp64)                                                                                           \
-            ffbs_wide_kernel<double, n, false><<<grid, WideGeo<double, n>::NT, WideGeo<double, n>::BYTES, s>>>(st, fl); \
-        else if (fl.ckpt_K > 0)                                                                            \
-            ffbs_wide_kernel<float, n, true><<<grid, WideGeo<float, n>::NT, WideGeo<float, n>::BYTES, s>>>(st, fl);     \
-        else                                                                                                \
-            ffbs_wide_kernel<float, n, false><<<grid, WideGeo<float, n>::NT, WideGeo<float, n>::BYTES, s>>>(st, fl);    \
-        return cudaGetLastError();
-        HQMC_WIDE_SIZES(HQMC_CASE)
-#undef HQMC_CASE
-        default: return cudaErrorInvalidValue;
-    }
+    return fl.gauss ? launch_ffbs_wide_g(L, fp64, st, fl, grid, s) : wide_launch_dispatch<false>(L, fp64, st, fl, grid, s);
 }
 
 }  // namespace hqmc

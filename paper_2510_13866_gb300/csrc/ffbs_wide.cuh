@@ -13,7 +13,7 @@
 // is one f32x2 operand, so complex adds and constant products issue as packed instructions.  No thread shares a line with another, so the FFT needs no cross-thread
 // exchange: the only data movement is the transpose.  The FMA pipe does the same work per
 // flop on scalars as on packed pairs, and a line per thread keeps the register count low
-// enough for three 128-thread CTAs per SM at L = 128.
+// enough for two 128-thread CTAs per SM at L = 128.
 //
 // Reductions over a worldline's lines (normaliser, maximum, row-total scan) are shuffles
 // over the lanes of one worldline (offsets WPC .. 16) and a fixed-order sum of the warps'
@@ -155,8 +155,11 @@ __device__ __forceinline__ T wl_warp_max(T v) {
 }
 
 // CKPT: f kept every fl.ckpt_K positions and recomputed per segment in the backward pass
-// (FP32 only); the streaming instantiation carries none of that code.
-template <typename T, int L, bool CKPT>
+// (FP32 only); the streaming instantiation carries none of that code.  GAUSS: the class
+// holds Gaussian-field chains (U < 0), whose potentials are read from the sigma field's
+// tables and whose log-weight estimate is summed in the backward pass; the Hirsch-only
+// instantiation carries none of that code.
+template <typename T, int L, bool CKPT, bool GAUSS>
 __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_wide_kernel(DevState st, FfbsLaunch fl) {
     using G = WideGeo<T, L>;
     constexpr int WPC = G::WPC, NT = G::NT, NW = G::NW, CH = G::CH, LP = G::LP, N = L * L;
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             const int xs = owner(0)[l0];
             const int sx = xs % L, sy = xs / L;
             T wv;
-            if (cd.gauss) wv = gauss_line<T>(st, cd, false, l0, sy)[sx];
+            if (GAUSS && cd.gauss) wv = gauss_line<T>(st, cd, false, l0, sy)[sx];
             else wv = ((srow[((long long)l0 * L + sy) * wpl + (sx >> 5)] >> (sx & 31)) & 1u) ? wp : wm;
 #pragma unroll
             for (int r = 0; r < L; ++r) v[r] = (has && p == sy && r == sx) ? wv : T(0);
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             const T sc = fbits<T>::pow2(-e);
             const int l1 = slice_of(i + 1);
             // the new layout is C (lines = x) when i is even: the field by columns
-            if (cd.gauss) {
+            if (GAUSS && cd.gauss) {
                 const T *wl_ = gauss_line<T>(st, cd, (i & 1) == 0, l1, p);
 #pragma unroll
                 for (int r = 0; r < L; ++r) v[r] *= wl_[r] * sc;
@@ -338,9 +341,9 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             return e;
         };
         const int K = CKPT ? fl.ckpt_K : 0;  // 0: every f streamed; else f kept every K positions
-        // Gaussian-field units: sum over interior positions of max alpha / alpha at the
-        // worldline's current site there (see the log-weight estimate below)
-        T ksum = T(0);
+        // Gaussian-field units keep max_y alpha_i(y) of every interior position i (at the
+        // scale of the stored f_i) after the worldline's f storage, for the backward pass
+        T *aux = slot + (fl.slot_elems / WPC - fl.len_max);
         for (int i = 0; i < len; ++i) {
             if (has) {
                 if (K == 0) {
@@ -351,24 +354,21 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             }
             const T s = conv_sum();
             if (i < len - 1) {
-                if (cd.gauss) {
-                    // v = alpha of position i + 1 (layout C if i + 1 is odd)
-                    const bool oc = (i & 1) == 0;
-                    const int xo = owner(i + 1)[slice_of(i + 1)];
-                    const int own = oc ? xo % L : xo / L, reg = oc ? xo / L : xo % L;
+                T top = T(0);
+                if (GAUSS && cd.gauss) {
+                    // v = alpha of position i + 1: its largest value over the worldline
                     T mx = T(0);
 #pragma unroll
                     for (int r = 0; r < L; ++r) mx = v[r] > mx ? v[r] : mx;
                     mx = wl_warp_max<WPC>(mx);
                     if (lane < WPC) wmx[warp * WPC + lane] = mx;
-                    if (p == own) endv[2 * WPC + w] = reg_select<L>(v, reg);
                     __syncthreads();
-                    T top = wmx[w];
+                    top = wmx[w];
                     for (int k = 1; k < NW; ++k) top = wmx[k * WPC + w] > top ? wmx[k * WPC + w] : top;
-                    const T a = endv[2 * WPC + w];
-                    ksum += a > T(0) ? top / a : T(__int_as_float(0x7f800000));
                 }
-                esum += renorm_w(i, s, true);
+                const int e = renorm_w(i, s, true);
+                esum += e;
+                if ((GAUSS && cd.gauss) && has && p == 0) aux[i + 1] = top * fbits<T>::pow2(-e);
             } else {
                 // alpha_{l0+len}(x_{l0+len}): the final layout is C if len is odd; its
                 // largest value gives kappa = top / end
@@ -402,14 +402,15 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                     for (int k = 1; k < NW; ++k) top = wmx[k * WPC + tid] > top ? wmx[k * WPC + tid] : top;
                     endv[WPC + tid] = top;
                 }
-                if (p == 0) {
-                    ibuf[9 + w] = esum;
-                    endv[3 * WPC + w] = ksum;
-                }
+                if (p == 0) ibuf[9 + w] = esum;
                 __syncthreads();
             }
         }
-        if (tid == 0) {
+        // the unit's log-weights and their error estimates (endv[3 WPC + k]: the Gaussian-field
+        // sum of worldline k from the backward pass); Hirsch units book them after the forward
+        // pass, Gaussian-field units after the backward pass
+        auto book = [&]() {
+            if (tid != 0) return;
             // log-weights of the block; with several blocks, the group's last finished block
             // sums the partials in block order (the same bits whichever finishes last)
             const double ln2 = 0.69314718055994530942;
@@ -418,11 +419,11 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             for (int k = 0; k < nwl; ++k) {
                 const T fin = endv[k], top = endv[WPC + k];
                 part[k] = double(ibuf[9 + k]) * ln2 + log(double(fin));
-                // Hirsch units: len x the end concentration; Gaussian units: the interior
-                // concentrations summed, plus the end's
+                // Hirsch units: len x the end concentration; Gaussian units: the concentrations
+                // at the drawn sites of positions 1 .. len-1, plus the end's
                 const double kap = double(top) / double(fin);
                 err[k] = !(fin > T(0)) ? inf
-                         : cd.gauss ? logw_err_estimate<T>((double(endv[3 * WPC + k]) + kap) / len, len, L, false)
+                         : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(endv[3 * WPC + k]) + kap) / len, len, L, false)
                                     : logw_err_estimate<T>(kap, len, L, false);
                 if (!(fin > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             }
@@ -462,7 +463,8 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                     *done = 0u;  // ready for the next sweep
                 }
             }
-        }
+        };
+        if (!(GAUSS && cd.gauss)) book();
 
         // ---- backward sampling ----
         // slice i of the slots -> xbuf: R slices (i even) chunk for chunk, C slices (i odd)
@@ -513,6 +515,17 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
         float ek = 0.f;
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
+        // Gaussian-field units: sum over positions i of max_y alpha_i(y) / alpha_i(x_i) at the
+        // drawn sites (alpha_i = f_i / W_i).  The draws follow the unit's posterior, under
+        // which the mean of this ratio is max alpha_i sum_y beta_i(y) / <alpha_i, beta_i>
+        // (beta_i the backward message from the held end): the factor by which a rounding
+        // error of the size of max alpha_i at slice i reaches the log-weight.  The three
+        // values of a draw are loaded at once and used one position later.
+        T kin = T(0), pf = T(0), pwv = T(0), pm = T(0);
+        bool pend = false;
+        auto take = [&]() {
+            if (pend) kin += pf > T(0) ? pm * pwv / pf : T(1) / T(0);
+        };
         for (int i = len - 1; i >= 1; --i) {
             int lb = l0 + i;
             if (lb >= M) lb -= M;
@@ -634,14 +647,79 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                 ek += hl[(cx - nxt % L + L) % L] + hl[(cy - nxt / L + L) % L];
                 owner(i)[lb] = int16_t(nxt);
                 atomicAdd(hist_s + (long long)lb * N + nxt, 1);
+                if (GAUSS && cd.gauss) {
+                    take();
+                    // element nxt of position i in the writer's layout (R for even i: line = y,
+                    // register = x; C for odd i)
+                    const bool ev = (i & 1) == 0;
+                    const int r = ev ? nxt % L : nxt / L, q = ev ? nxt / L : nxt % L;
+                    pf = __ldcg(f_src(slot, i) + ((long long)(r / CH) * L + q) * CH + r % CH);
+                    pwv = gauss_line<T>(st, cd, false, lb, nxt / L)[nxt % L];
+                    pm = __ldcg(aux + i);
+                    pend = true;
+                }
             }
             cur = nxt;
+        }
+        if (GAUSS && cd.gauss) {
+            if (has && p == 0) {
+                take();
+                endv[3 * WPC + w] = kin;
+            }
+            __syncthreads();
+            book();
         }
         if (has && p == 0) {
             // link x_{l0} -> x_{l0+1}
             ek += hl[(cur % L - sx + L) % L] + hl[(cur / L - sy + L) % L];
             atomicAdd(&st.meas[c].link_sum, double(ek) * chain_sign(st, c));
         }
+    }
+}
+
+#define HQMC_WIDE_SIZES(X) X(48) X(64) X(128)
+
+// host side, per Gaussian flag: raise the kernels' shared-memory limits and return the
+// residency of the streaming instantiation; launch the class's instantiation (the limit is
+// raised beforehand, never during stream capture)
+template <typename T, int L, bool G>
+cudaError_t wide_occ(int *blocks) {
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t e = raise_smem_limit(ffbs_wide_kernel<T, L, true, G>, WideGeo<T, L>::BYTES);
+        if (e != cudaSuccess) return e;
+    }
+    auto k = ffbs_wide_kernel<T, L, false, G>;
+    cudaError_t e = raise_smem_limit(k, WideGeo<T, L>::BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, WideGeo<T, L>::NT, WideGeo<T, L>::BYTES);
+}
+
+template <bool G>
+cudaError_t wide_occ_dispatch(int L, bool fp64, int *blocks) {
+    switch (L) {
+#define HQMC_CASE(n) \
+    case n: return fp64 ? wide_occ<double, n, G>(blocks) : wide_occ<float, n, G>(blocks);
+        HQMC_WIDE_SIZES(HQMC_CASE)
+#undef HQMC_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool G>
+cudaError_t wide_launch_dispatch(int L, bool fp64, const DevState &st, const FfbsLaunch &fl, int grid, cudaStream_t s) {
+    switch (L) {
+#define HQMC_CASE(n)                                                                                           \
+    case n:                                                                                                    \
+        if (fp64)                                                                                              \
+            ffbs_wide_kernel<double, n, false, G><<<grid, WideGeo<double, n>::NT, WideGeo<double, n>::BYTES, s>>>(st, fl); \
+        else if (fl.ckpt_K > 0)                                                                               \
+            ffbs_wide_kernel<float, n, true, G><<<grid, WideGeo<float, n>::NT, WideGeo<float, n>::BYTES, s>>>(st, fl);     \
+        else                                                                                                   \
+            ffbs_wide_kernel<float, n, false, G><<<grid, WideGeo<float, n>::NT, WideGeo<float, n>::BYTES, s>>>(st, fl);    \
+        return cudaGetLastError();
+        HQMC_WIDE_SIZES(HQMC_CASE)
+#undef HQMC_CASE
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -4,7 +4,6 @@
 
 namespace hqmc {
 
-#define HQMC_WIDE_SIZES(X) X(48) X(64) X(128)
 
 template <typename T, int L>
 static cudaError_t gw_occ(int *blocks) {

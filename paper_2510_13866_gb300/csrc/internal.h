@@ -121,7 +121,7 @@ struct FfbsLaunch {
     int total_units;
     int len_max;               // longest block in the class (scratch slot size, slices)
     void *scratch;             // slots of len_max * L * L complex values
-    long long slot_elems;      // complex elements per slot
+    long long slot_elems;      // elements per group slot (f storage, then len_max maxima)
     unsigned *next_unit;       // work counter: groups take units in order (zeroed per launch)
     int stencil;               // line convolutions by the periodic stencil instead of the FFT
     int general;               // some chain has FFBS blocks B < M, or the context has used

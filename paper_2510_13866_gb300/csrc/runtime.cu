@@ -77,6 +77,10 @@ struct LClass {
     // seg_off of a worldline's slot of wl_elems floats (ckpt_K = 0: every f streamed)
     int ckpt_K = 0;
     long long seg_off = 0, wl_elems = 0;
+    // FFBS slot per group, in the kernel's elements (pairs for L <= 32, scalars of the CTA's
+    // worldlines for wide): the f storage of each worldline, then len_max per-position maxima
+    // of the forward messages (Gaussian-field units), padded to whole 16-byte chunks
+    long long slot_elems = 0;
     size_t cls_off = 0;    // device offset of the class arrays
 };
 
@@ -462,20 +466,26 @@ int plan_layout(hqmc_ctx *c, size_t *total) {
         k.grid = std::max(1, grid);
         k.groups = (long long)k.grid * gpc;
         // f slots: a worldline pair per group (L <= 32), or the CTA's worldlines (wide)
-        const size_t elem = is_big(k.L) ? size_t(ffbs_wide_wpc(k.L)) * (f64 ? 8 : 4) : (f64 ? 16 : 8);
-        k.scratch_bytes = size_t(k.groups) * k.len_max * k.L * k.L * elem;
+        const long long N = (long long)k.L * k.L;
+        // elements per 16-byte chunk: pairs of FP32 (one for odd L, whose chunks are 8 bytes),
+        // FP64 pairs, wide scalars
+        const long long ch = is_big(k.L) ? (f64 ? 2 : 4) : (f64 || (k.L & 1)) ? 1 : 2;
+        const long long aux = (k.len_max + ch - 1) / ch * ch;
+        long long per_wl = (long long)k.len_max * N;
         k.ckpt_K = 0;
         if (is_big(k.L) && !f64 && c->fstore != HQMC_FSTORE_STREAM) {
             // checkpoints every K positions (BF16: two per float) then a K-slice segment
-            const long long N = (long long)k.L * k.L;
             const int K = c->fstride > 0 ? std::min(c->fstride, k.len_max)
                                          : std::max(1, int(std::ceil(std::sqrt(double(k.len_max)))));
             const long long nseg = (k.len_max + K - 1) / K;
             k.ckpt_K = K;
             k.seg_off = (c->fstore == HQMC_FSTORE_BF16) ? nseg * N / 2 : nseg * N;
             k.wl_elems = k.seg_off + (long long)K * N;
-            k.scratch_bytes = size_t(k.groups) * ffbs_wide_wpc(k.L) * size_t(k.wl_elems) * 4;
+            per_wl = k.wl_elems;
         }
+        k.slot_elems = (per_wl + aux) * (is_big(k.L) ? ffbs_wide_wpc(k.L) : 1);
+        const size_t elem = is_big(k.L) ? (f64 ? 8 : 4) : (f64 ? 16 : 8);
+        k.scratch_bytes = size_t(k.groups) * size_t(k.slot_elems) * elem;
         k.scratch_off = take(k.scratch_bytes);
     }
     *total = round_up(off, 256);
@@ -696,12 +706,10 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
         fl.general = (cl.total_units != cl.total_pairs || c->perm_used) ? 1 : 0;
         fl.stencil = (c->conv == HQMC_CONV_STENCIL && !is_big(cl.L)) ? 1 : 0;
         fl.scratch = c->base + cl.scratch_off;
-        // slot per group: pair elements (L <= 32) or scalars of the CTA's worldlines (wide)
-        fl.slot_elems = (long long)cl.len_max * cl.L * cl.L * (is_big(cl.L) ? ffbs_wide_wpc(cl.L) : 1);
+        fl.slot_elems = cl.slot_elems;
         fl.ckpt_K = cl.ckpt_K;
         fl.ckpt_bf16 = c->fstore == HQMC_FSTORE_BF16 ? 1 : 0;
         fl.seg_off = cl.seg_off;
-        if (cl.ckpt_K > 0) fl.slot_elems = cl.wl_elems * ffbs_wide_wpc(cl.L);
         cudaStream_t s = k == 0 ? st : c->aux[k - 1];
         HQMC_CUDA(c, cudaMemsetAsync(fl.next_unit, 0, sizeof(unsigned), s));
         const int wpc = default_wpc(c, cl.L);

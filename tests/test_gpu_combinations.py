@@ -18,12 +18,12 @@ to about eps kappa per block.  Strong Gaussian fields (U < 0 with large |U| dtau
 kappa = 1e4 to 1e15 within two sweeps.  The library reports an error estimate per
 log-weight (hqmc_logw_error: eps log2(N) len kappa per block, with its own kappa) and
 counts those above the tolerance (hqmc_obs.n_inexact).  Under a Gaussian field the message
-can concentrate more at interior slices than at the end, so there the library sums the
-concentration max_y alpha_i(y) / alpha_i(x_i) over the unit's slices i (at the sites of
-the path it resamples) instead of taking len times the end's.  Every log-weight it does
-not flag must meet the plain tolerance; a flagged one must lie within its estimate; and on
-a single-block unit the library's kappa (its interior sum, for a Gaussian field) must be
-the oracle's.
+can concentrate more at interior slices than at the end, so there the library sums
+max_y alpha_i(y) / alpha_i(x_i) over the unit's positions i at the sites x_i it has just
+drawn, instead of taking len times the end's.  Every log-weight it does not flag must meet
+the plain tolerance; a flagged one must lie within its estimate; and on a single-block unit
+the library's kappa (for a Gaussian field, its sum over the drawn path) must be the
+oracle's.
 """
 import numpy as np
 import pytest
@@ -101,19 +101,19 @@ def unit_kappa(orc, W, a, block, sg, p):
     return kap
 
 
-def unit_kappa_sum(orc, W, a, sg, p, x_old):
-    """Gaussian-field form for a closed single-block unit: the concentration
-    max_y alpha_i(y) / alpha_i(x_i) summed over the positions i = 1..M-1 at the sites of the
-    path before the sweep, plus the end's."""
+def unit_kappa_sum(orc, W, a, sg, p, x_new):
+    """Gaussian-field form for a closed single-block unit: max_y alpha_i(y) / alpha_i(x_i)
+    summed over the positions i = 1..M, at the sites x_new the GPU drew (position M is the
+    held end)."""
     L, M, N = orc.L, orc.M, orc.N
     g, _ = oracle.g_table(L, orc.t, orc.dtau)
     G = np.fft.fft2(np.outer(g, g))
-    xa = int(x_old[sg, p, a])
+    xa = int(x_new[sg, p, a])
     _, f = oracle.filter_block(L, M, g, W[sg], a, M, xa, xa, want_f=True)
     tot = 0.0
     for i in range(1, M + 1):
         al = np.real(np.fft.ifft2(np.fft.fft2(f[(a + i - 1) % M].reshape(L, L)) * G)).reshape(-1)
-        tot += al.max() / max(al[int(x_old[sg, p, (a + i) % M])], 1e-300)
+        tot += al.max() / max(al[int(x_new[sg, p, (a + i) % M])], 1e-300)
     return tot
 
 
@@ -158,7 +158,6 @@ def test_random_combination_matches_oracle(case):
             if not live[c]:
                 continue
             W = slice_potentials(orc)  # the fields this sweep filters with
-            x_old = orc.x.copy()
             if perm:
                 ref = orc.perm_sweep(want_margin=True, block=block)
                 p_gpu, sign = lat.get_perm(c)
@@ -197,7 +196,7 @@ def test_random_combination_matches_oracle(case):
                 if orc.gauss:
                     if perm:
                         continue  # the unit's path crosses worldlines at the permuted boundary
-                    kap = unit_kappa_sum(orc, W, a, sg, p, x_old) / orc.M
+                    kap = unit_kappa_sum(orc, W, a, sg, p, x) / orc.M
                 else:
                     kap = unit_kappa(orc, W, a, block, sg, p)
                 if kap < 1e-3 / EPS[prec]:
@@ -278,10 +277,10 @@ def test_autotune_keeps_results_with_every_option():
 
 def test_zz_error_estimate_calibration():
     """Distribution of |log-weight error| / estimate over the random combinations above (run
-    with -s to print it).  The FP32 FFT filter's errors stay within their estimate: the
-    estimate eps log2(N) len kappa uses the end concentration for every slice, and in FP32
-    the rounding at the end dominates.  FP64 is printed, not bounded: strong Gaussian fields
-    concentrate the message more at interior slices than at the end."""
+    with -s to print it).  The FP32 FFT filter's errors stay within their estimate (for
+    Hirsch fields eps log2(N) len kappa with the end concentration standing in for every
+    slice's; for Gaussian fields the concentrations at the drawn sites summed).  FP64 is
+    printed, not bounded."""
     if not RATIOS:
         pytest.skip("the random combinations did not run in this session")
     print()
