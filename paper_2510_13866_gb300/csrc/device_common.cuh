@@ -135,10 +135,11 @@ struct cvec {
     V re, im;
 };
 
-// One FP32 worldline per thread: a complex value's (re, im) travel as one f32x2 pair, so a
-// complex add is one FADD2 and a product with a constant one FMUL2 + one FFMA2.
+// One FP32 worldline per thread: a complex add or subtract takes (re, im) as one f32x2
+// pair (one FADD2).  Products that cross the halves (re with im) stay scalar: packed forms
+// that swapped the two halves of a pair gave results that depended on register allocation
+// and differed between identical runs on sm_103a.
 __device__ __forceinline__ float2 pk(const cvec<float> &a) { return make_float2(a.re, a.im); }
-__device__ __forceinline__ float2 swp(const cvec<float> &a) { return make_float2(a.im, a.re); }
 __device__ __forceinline__ cvec<float> upk(float2 v) { return {v.x, v.y}; }
 
 template <typename V>
@@ -154,13 +155,9 @@ __device__ __forceinline__ cvec<V> cv_sub(cvec<V> a, cvec<V> b) {
 // multiply by +i (SGN > 0) or -i
 template <int SGN, typename V>
 __device__ __forceinline__ cvec<V> cv_muli(cvec<V> a) {
-    if constexpr (std::is_same<V, float>::value) {
-        // i (re, im) = (-im, re), -i (re, im) = (im, -re)
-        return upk(__fmul2_rn(swp(a), SGN > 0 ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f)));
-    } else {
-        if constexpr (SGN > 0) return {vsub(vzero(a.im), a.im), a.re};
-        else return {a.im, vsub(vzero(a.re), a.re)};
-    }
+    // i (re, im) = (-im, re), -i (re, im) = (im, -re)
+    if constexpr (SGN > 0) return {vsub(vzero(a.im), a.im), a.re};
+    else return {a.im, vsub(vzero(a.re), a.re)};
 }
 
 // ---------------------------------------------------------------------------------
@@ -267,10 +264,7 @@ __device__ __forceinline__ cvec<V> twiddle(cvec<V> v) {
         constexpr T c = T(ct::cos2pi(k, NN));
         constexpr T s = T(SGN * ct::sin2pi(k, NN));
         // (re + i im)(c + i s) = (c re - s im) + i (s re + c im)
-        if constexpr (std::is_same<V, float>::value)
-            return upk(__ffma2_rn(pk(v), make_float2(c, c), __fmul2_rn(swp(v), make_float2(-s, s))));
-        else
-            return {vfma(v.re, splat<V>(c), vmul(v.im, splat<V>(-s))), vfma(v.re, splat<V>(s), vmul(v.im, splat<V>(c)))};
+        return {vfma(v.re, splat<V>(c), vmul(v.im, splat<V>(-s))), vfma(v.re, splat<V>(s), vmul(v.im, splat<V>(c)))};
     }
 }
 
@@ -290,11 +284,10 @@ __device__ __forceinline__ void dft3(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2) {
     cvec<V> base, rot;
     if constexpr (std::is_same<V, float>::value) {
         base = upk(__ffma2_rn(pk(sum), make_float2(h, h), pk(a0)));
-        rot = upk(__fmul2_rn(swp(dif), make_float2(-s, s)));  // i s (a1 - a2)
     } else {
         base = {vfma(sum.re, splat<V>(h), a0.re), vfma(sum.im, splat<V>(h), a0.im)};
-        rot = {vmul(dif.im, splat<V>(-s)), vmul(dif.re, splat<V>(s))};  // i s (a1 - a2)
     }
+    rot = {vmul(dif.im, splat<V>(-s)), vmul(dif.re, splat<V>(s))};  // i s (a1 - a2)
     a0 = cv_add(a0, sum);
     a1 = cv_add(base, rot);
     a2 = cv_sub(base, rot);
@@ -306,12 +299,7 @@ __device__ __forceinline__ void dft4(cvec<V> &a0, cvec<V> &a1, cvec<V> &a2, cvec
     a0 = cv_add(s02, s13);
     a2 = cv_sub(s02, s13);
     // a1 = d02 + (SGN i) d13, a3 = d02 - (SGN i) d13, with the rotation folded into add/sub
-    if constexpr (std::is_same<V, float>::value) {
-        // (SGN i) d13 = (d13.im, d13.re) . (-SGN, SGN)
-        const float2 p = make_float2(-float(SGN), float(SGN)), m = make_float2(float(SGN), -float(SGN));
-        a1 = upk(__ffma2_rn(swp(d13), p, pk(d02)));
-        a3 = upk(__ffma2_rn(swp(d13), m, pk(d02)));
-    } else if constexpr (SGN > 0) {
+    if constexpr (SGN > 0) {
         a1 = {vsub(d02.re, d13.im), vadd(d02.im, d13.re)};
         a3 = {vadd(d02.re, d13.im), vsub(d02.im, d13.re)};
     } else {
@@ -501,14 +489,20 @@ __device__ __forceinline__ void conv_line_1fft(T (&v)[L], const T *mixc) {
                 constexpr int k = decltype(KI)::value;
                 constexpr int kp = (n - k) % n;
                 auto mixk = [&](const cvec<T> &zk, const cvec<T> &zp, int kk) -> cvec<T> {
+                    T a, na, b, nb;
                     if constexpr (std::is_same<T, float>::value) {
                         const float4 c4 = reinterpret_cast<const float4 *>(mixc)[kk];
-                        return upk(__ffma2_rn(pk(zk), make_float2(c4.x, c4.y),
-                                              __fmul2_rn(swp(zp), make_float2(c4.z, c4.w))));
+                        a = c4.x;
+                        na = c4.y;
+                        b = c4.z;
+                        nb = c4.w;
                     } else {
-                        const T a = mixc[4 * kk], na = mixc[4 * kk + 1], b = mixc[4 * kk + 2], nb = mixc[4 * kk + 3];
-                        return {fma(zk.re, a, zp.im * b), fma(zk.im, na, zp.re * nb)};
+                        a = mixc[4 * kk];
+                        na = mixc[4 * kk + 1];
+                        b = mixc[4 * kk + 2];
+                        nb = mixc[4 * kk + 3];
                     }
+                    return {fma(zk.re, a, zp.im * b), fma(zk.im, na, zp.re * nb)};
                 };
                 if constexpr (k == kp) {
                     z[k] = mixk(z[k], z[k], k);

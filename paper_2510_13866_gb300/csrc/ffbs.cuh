@@ -549,22 +549,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
         }
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
-        // Gaussian-field units: sum over positions i of max_y alpha_i(y) / alpha_i(x_i) at the
-        // drawn sites (alpha_i = f_i / W_i).  The draws follow the unit's posterior, under
-        // which the mean of this ratio is max alpha_i sum_y beta_i(y) / <alpha_i, beta_i>
-        // (beta_i the backward message from the held end): the factor by which a rounding
-        // error of the size of max alpha_i at slice i reaches the log-weight.  The three
-        // values of a draw are loaded at once and used one position later.
+        // Gaussian-field units: sum over positions i of E[max_y alpha_i(y) / alpha_i(x_i) | x_{i+1}]
+        // = max alpha_i sum_y W_i(y) G(x_{i+1} - y) / S_i, S_i = sum_y f_i(y) G(x_{i+1} - y) the
+        // draw's total.  Under the unit's posterior its mean is max alpha_i sum_y beta_i(y) /
+        // <alpha_i, beta_i> (beta_i the backward message from the held end): the factor by which
+        // a rounding error of the size of max alpha_i at slice i reaches the log-weight.
         T kin0 = T(0), kin1 = T(0);
-        T pf0 = T(0), pf1 = T(0), pw0 = T(0), pw1 = T(0), pm0 = T(0), pm1 = T(0);
-        bool pend = false;
-        auto take = [&]() {
-            if (pend) {
-                const T inf = T(1) / T(0);
-                kin0 += pf0 > T(0) ? pm0 * pw0 / pf0 : inf;
-                kin1 += pf1 > T(0) ? pm1 * pw1 / pf1 : inf;
-            }
-        };
         for (int i = len - 1; i >= 1; --i) {
             int lb = l0 + i;
             if (lb >= M) lb -= M;
@@ -643,6 +633,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             }
             const T S0 = __shfl_sync(gmask, in0, L - 1, GW);
             const T S1 = __shfl_sync(gmask, in1, L - 1, GW);
+            if constexpr (GAUSS) {
+                if (cd.gauss) {
+                    // sum_y W_i(y) G(x_{i+1} - y) over row gl of W (the same field for both spins)
+                    V Q = vzero(v[0]);
+                    if (active) {
+                        const T *wrow = gauss_line<T>(st, cd, false, lb, gl);
+#pragma unroll 4
+                        for (int ix = 0; ix < L; ++ix) Q = vfma(vsplat(wrow[ix]), wx[ix], Q);
+                        Q = vmul(Q, gy);
+                    }
+                    const T q0 = group_sum<GW>(Q.x, gmask), q1 = group_sum<GW>(Q.y, gmask);
+                    const V am = __ldcg(aux + i);
+                    const T inf = T(1) / T(0);
+                    kin0 += S0 > T(0) ? am.x * q0 / S0 : inf;
+                    kin1 += S1 > T(0) ? am.y * q1 / S1 : inf;
+                }
+            }
             const T t0 = draw_target<T>(uw0, S0);
             const T t1 = draw_target<T>(uw1, S1);
             // the row that holds the crossing (the first row whose total exceeds what remains
@@ -728,34 +735,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
                     atomicAdd(hist_s + (long long)lb * N + nxt1, 1);
                 }
             }
-            if constexpr (GAUSS) {
-                if (cd.gauss && gl == 0) {
-                    take();
-                    // element x of position i in the writer's layout (R for even i: lane = iy,
-                    // register = ix; C for odd i)
-                    const bool ev = (i & 1) == 0;
-                    auto fat = [&](int x) {
-                        const int r = ev ? x % L : x / L, q = ev ? x / L : x % L;
-                        return slot + (long long)i * N + ((long long)(r / CH) * L + q) * CH + r % CH;
-                    };
-                    pf0 = __ldcg(&fat(nxt0)->x);
-                    pf1 = __ldcg(&fat(nxt1)->y);
-                    pw0 = gauss_line<T>(st, cd, false, lb, nxt0 / L)[nxt0 % L];
-                    pw1 = gauss_line<T>(st, cd, false, lb, nxt1 / L)[nxt1 % L];
-                    const V am = __ldcg(aux + i);
-                    pm0 = am.x;
-                    pm1 = am.y;
-                    pend = true;
-                }
-            }
             cur0 = nxt0;
             cur1 = nxt1;
         }
         if constexpr (GAUSS) {
-            if (cd.gauss) {
-                if (gl == 0) take();
-                book(double(kin0), double(kin1));
-            }
+            if (cd.gauss) book(double(kin0), double(kin1));
         }
         if (gl == 0) {
             // link x_{l0} -> x_{l0+1}

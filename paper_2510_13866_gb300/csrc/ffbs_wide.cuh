@@ -9,11 +9,11 @@
 // is the line convolution of every line in registers (conv_line_1fft: a half-length complex
 // FFT, the spectral mix of a real line, and the same FFT code again for the inverse), one
 // transpose per worldline through shared memory, and the line convolution along the other
-// direction; the layout alternates between slices.  In FP32 a complex value's (re, im) pair
-// is one f32x2 operand, so complex adds and constant products issue as packed instructions.  No thread shares a line with another, so the FFT needs no cross-thread
-// exchange: the only data movement is the transpose.  The FMA pipe does the same work per
-// flop on scalars as on packed pairs, and a line per thread keeps the register count low
-// enough for two 128-thread CTAs per SM at L = 128.
+// direction; the layout alternates between slices.  In FP32 the complex adds and subtracts
+// take a value's (re, im) as one f32x2 operand; products that cross the halves stay scalar.
+// No thread shares a line with another, so the FFT needs no cross-thread exchange: the only
+// data movement is the transpose.  A line per thread keeps the register count low enough
+// for two 128-thread CTAs per SM at L = 128.
 //
 // Reductions over a worldline's lines (normaliser, maximum, row-total scan) are shuffles
 // over the lanes of one worldline (offsets WPC .. 16) and a fixed-order sum of the warps'
@@ -515,17 +515,12 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
         float ek = 0.f;
         int cached = -1;
         uint64_t wd0 = 0, wd1 = 0, wd2 = 0, wd3 = 0;
-        // Gaussian-field units: sum over positions i of max_y alpha_i(y) / alpha_i(x_i) at the
-        // drawn sites (alpha_i = f_i / W_i).  The draws follow the unit's posterior, under
-        // which the mean of this ratio is max alpha_i sum_y beta_i(y) / <alpha_i, beta_i>
-        // (beta_i the backward message from the held end): the factor by which a rounding
-        // error of the size of max alpha_i at slice i reaches the log-weight.  The three
-        // values of a draw are loaded at once and used one position later.
-        T kin = T(0), pf = T(0), pwv = T(0), pm = T(0);
-        bool pend = false;
-        auto take = [&]() {
-            if (pend) kin += pf > T(0) ? pm * pwv / pf : T(1) / T(0);
-        };
+        // Gaussian-field units: sum over positions i of E[max_y alpha_i(y) / alpha_i(x_i) | x_{i+1}]
+        // = max alpha_i sum_y W_i(y) G(x_{i+1} - y) / S_i, S_i = sum_y f_i(y) G(x_{i+1} - y) the
+        // draw's total.  Under the unit's posterior its mean is max alpha_i sum_y beta_i(y) /
+        // <alpha_i, beta_i> (beta_i the backward message from the held end): the factor by which
+        // a rounding error of the size of max alpha_i at slice i reaches the log-weight.
+        T kin = T(0);
         for (int i = len - 1; i >= 1; --i) {
             int lb = l0 + i;
             if (lb >= M) lb -= M;
@@ -606,6 +601,15 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             }
             const T ex = base + inc - P;
             const T t = draw_target<T>(ubuf[w], Stot);
+            if (GAUSS && cd.gauss) {
+                // sum_y W_i(y) G(x_{i+1} - y): row p of W against the x-weights
+                const T *wrow = gauss_line<T>(st, cd, false, lb, p);
+                T Q = T(0);
+#pragma unroll 4
+                for (int x = 0; x < L; ++x) Q = vfma(wrow[x], wx[x], Q);
+                const T qs = wl_sum(Q * g2[p - cy + L]);
+                if (has && p == 0) kin += Stot > T(0) ? __ldcg(aux + i) * qs / Stot : T(1) / T(0);
+            }
             const T rem = t - ex;
             if (has) {
                 int n = 0;
@@ -647,25 +651,11 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                 ek += hl[(cx - nxt % L + L) % L] + hl[(cy - nxt / L + L) % L];
                 owner(i)[lb] = int16_t(nxt);
                 atomicAdd(hist_s + (long long)lb * N + nxt, 1);
-                if (GAUSS && cd.gauss) {
-                    take();
-                    // element nxt of position i in the writer's layout (R for even i: line = y,
-                    // register = x; C for odd i)
-                    const bool ev = (i & 1) == 0;
-                    const int r = ev ? nxt % L : nxt / L, q = ev ? nxt / L : nxt % L;
-                    pf = __ldcg(f_src(slot, i) + ((long long)(r / CH) * L + q) * CH + r % CH);
-                    pwv = gauss_line<T>(st, cd, false, lb, nxt / L)[nxt % L];
-                    pm = __ldcg(aux + i);
-                    pend = true;
-                }
             }
             cur = nxt;
         }
         if (GAUSS && cd.gauss) {
-            if (has && p == 0) {
-                take();
-                endv[3 * WPC + w] = kin;
-            }
+            if (has && p == 0) endv[3 * WPC + w] = kin;
             __syncthreads();
             book();
         }
