@@ -346,7 +346,7 @@ def observables(lat, shapes, sweeps, open_path=True):
 
 
 def kernel_source_digest(workload="L32"):
-    """Digest of the sources the workload's FFBS kernels compile from (the warp kernel for
+    """Digest of the sources the workload's FFBS kernels compile from (the register kernel for
     L <= 32, the wide kernel too otherwise): the committed DRAM counters apply only to them."""
     import hashlib
 
@@ -514,7 +514,8 @@ def main():
                 traffic_note = "kernel changed since the committed DRAM counters were taken"
         except Exception:
             traffic = None
-    kname = "ffbs_kernel<float,32>" if args.workload == "L32" else "FFBS launches (all sizes)"
+    kname = {"L32": "ffbs_kernel<float,32>", "L64": "ffbs_wide_kernel<float,64>",
+             "L128": "ffbs_wide_kernel<float,128>"}.get(args.workload, "FFBS launches (all sizes)")
     roofline = {"bound": "hbm" if ckpt_note is None else "alu", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
                 "peak_source": peak_src, "kernel": kname, "kernel_ms": ffbs_avg, "gibbs_measure_ms": slice_avg,

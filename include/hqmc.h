@@ -220,11 +220,13 @@ int hqmc_sweep(hqmc_ctx *ctx, int n_sweeps, double *logw_out);
  * site that ends kappa = max_y alpha_end(y) / alpha_end(x_end) times below the largest
  * carries about eps log2(N) kappa from each slice.  The estimate of a block of len slices
  * is eps log2(N) len kappa for a Hirsch field (eps = 2^-24 in FP32, 2^-53 in FP64; the end
- * concentration stands in for every slice's) and eps log2(N) sum_i max_y alpha_i(y) /
- * alpha_i(x_i) for a Gaussian field, over the block's positions i at the sites x_i the
- * sweep drew (a strong Gaussian field concentrates the message more inside the block than
- * at its end; over the drawn path this sum has the mean that propagates slice i's rounding
- * to the log-weight), summed over the worldline's blocks.  With HQMC_CONV_STENCIL every
+ * concentration stands in for every slice's).  A strong Gaussian field concentrates the
+ * message more inside the block than at its end, so for a Gaussian field it is
+ * eps log2(N) (c sum_i E[max_y alpha_i(y) / alpha_i(x_i) | x_{i+1}] + kappa) over the block's
+ * interior positions i, given the sites x_{i+1} the sweep drew (over the posterior of the
+ * path these terms have the mean that carries slice i's rounding to the log-weight), with
+ * the calibration factor c = 1 in FP32 and 32 in FP64.  The estimates of a worldline's
+ * blocks are summed.  With HQMC_CONV_STENCIL every
  * output is a sum of non-negative terms that keeps its own relative accuracy and kappa is
  * replaced by 1.  A non-positive end value gives +inf.  Worldlines whose estimate exceeds
  * the precision's tolerance are counted in hqmc_obs.n_inexact; where this matters (strong

@@ -623,13 +623,13 @@ __host__ __device__ constexpr double logw_tolerance() { return sizeof(T) == 4 ? 
 // about eps log2(N) of the slice's largest value, so a site that ends kappa times below the
 // largest, kappa = max_y alpha_end(y) / alpha_end(x_end), carries a relative error of about
 // eps log2(N) kappa from each slice: eps log2(N) len kappa for a block of len slices, the end
-// concentration standing in for every slice's.  The stencil form sums non-negative terms, so
-// every site keeps its own relative accuracy and kappa is replaced by 1.  eps = 2^-24 (FP32),
-// 2^-53 (FP64).  A non-positive end value gives +inf.  Against the oracle's direct
-// convolution (48 random combinations and an equilibrated L = 32 state, 8604 log-weights)
-// the FP32 errors stay below 0.73 of it; FP64 errors under strong Gaussian fields (U < 0,
-// |U| dtau >= 0.4), whose messages concentrate at interior slices more than at the end,
-// exceed it by up to 1.3e-11 relative.
+// concentration standing in for every slice's (Hirsch fields).  The stencil form sums
+// non-negative terms, so every site keeps its own relative accuracy and kappa is replaced by
+// 1.  eps = 2^-24 (FP32), 2^-53 (FP64).  A non-positive end value gives +inf.  Against the
+// oracle's direct convolution (48 random combinations and an equilibrated L = 32 state) the
+// FP32 errors stay below 0.73 of it.  Gaussian-field units pass the sum over their slices
+// of a one-sample estimate of each slice's concentration (gauss_sum_factor below) plus the
+// end's, with len = 1.
 template <typename T>
 __device__ __forceinline__ double logw_err_estimate(double kappa, int len, int L, bool stencil) {
     const double eps = sizeof(T) == 4 ? 0x1.0p-24 : 0x1.0p-53;
@@ -637,6 +637,14 @@ __device__ __forceinline__ double logw_err_estimate(double kappa, int len, int L
     const double k = stencil ? 1.0 : kappa;
     return eps * log2n * double(len > 0 ? len : 1) * k;
 }
+
+// Calibration factor of the sampled part of the Gaussian-field estimate.  FP64 flags only
+// strongly concentrated units (the tolerance is 1e-12 against eps = 1.1e-16), where the
+// one-sample conditional mean of each slice's concentration spreads most: over 1108 FP64
+// log-weights of the random combinations the error reached 20.7 times the unscaled sum
+// (99th percentile 5.7), while FP32 stayed below 0.3 of it.
+template <typename T>
+__host__ __device__ constexpr double gauss_sum_factor() { return sizeof(T) == 4 ? 1.0 : 32.0; }
 
 // Ampere-style asynchronous global -> shared copies (16 or 8 bytes per lane).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {

@@ -463,10 +463,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             // the end's
             const double kap0 = double(top0) / double(fin0), kap1 = double(top1) / double(fin1);
             const double err0 = !(fin0 > T(0)) ? inf
-                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(kin0) + kap0) / len, len, L, STN)
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>(gauss_sum_factor<T>() * kin0 + kap0, STN ? len : 1, L, STN)
                                            : logw_err_estimate<T>(kap0, len, L, STN);
             const double err1 = !(fin1 > T(0)) ? inf
-                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(kin1) + kap1) / len, len, L, STN)
+                                : (GAUSS && cd.gauss) ? logw_err_estimate<T>(gauss_sum_factor<T>() * kin1 + kap1, STN ? len : 1, L, STN)
                                            : logw_err_estimate<T>(kap1, len, L, STN);
             // a log-weight whose estimate exceeds the tolerance is counted (hqmc_obs.n_inexact)
             auto flag = [&](double lwv, double e) {

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
                 // at the drawn sites of positions 1 .. len-1, plus the end's
                 const double kap = double(top) / double(fin);
                 err[k] = !(fin > T(0)) ? inf
-                         : (GAUSS && cd.gauss) ? logw_err_estimate<T>((double(endv[3 * WPC + k]) + kap) / len, len, L, false)
+                         : (GAUSS && cd.gauss) ? logw_err_estimate<T>(gauss_sum_factor<T>() * double(endv[3 * WPC + k]) + kap, 1, L, false)
                                     : logw_err_estimate<T>(kap, len, L, false);
                 if (!(fin > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             }

@@ -18,12 +18,12 @@ to about eps kappa per block.  Strong Gaussian fields (U < 0 with large |U| dtau
 kappa = 1e4 to 1e15 within two sweeps.  The library reports an error estimate per
 log-weight (hqmc_logw_error: eps log2(N) len kappa per block, with its own kappa) and
 counts those above the tolerance (hqmc_obs.n_inexact).  Under a Gaussian field the message
-can concentrate more at interior slices than at the end, so there the library sums
-max_y alpha_i(y) / alpha_i(x_i) over the unit's positions i at the sites x_i it has just
-drawn, instead of taking len times the end's.  Every log-weight it does not flag must meet
-the plain tolerance; a flagged one must lie within its estimate; and on a single-block unit
-the library's kappa (for a Gaussian field, its sum over the drawn path) must be the
-oracle's.
+can concentrate more at interior slices than at the end, so there the library sums, over
+the unit's positions i, the mean of max_y alpha_i(y) / alpha_i(x_i) given the site x_{i+1}
+it has just drawn (times a calibration factor in FP64), instead of taking len times the
+end's.  Every log-weight it does not flag must meet the plain tolerance; a flagged one must
+lie within its estimate; and on a single-block unit the library's kappa must be the one the
+oracle's messages give (for a Gaussian field, along the GPU's drawn path).
 """
 import numpy as np
 import pytest
@@ -36,6 +36,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-5, "fp64": 1e-12}
 EPS = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
+# the library's calibration factor of the sampled part of a Gaussian-field estimate
+GAUSS_FACTOR = {"fp32": 1.0, "fp64": 32.0}
 SIZES = (2, 3, 4, 6, 8, 12, 16, 24, 32, 48)
 
 
@@ -101,20 +103,29 @@ def unit_kappa(orc, W, a, block, sg, p):
     return kap
 
 
-def unit_kappa_sum(orc, W, a, sg, p, x_new):
-    """Gaussian-field form for a closed single-block unit: max_y alpha_i(y) / alpha_i(x_i)
-    summed over the positions i = 1..M, at the sites x_new the GPU drew (position M is the
-    held end)."""
+def unit_kappa_sum(orc, W, a, sg, p, x_new, factor):
+    """Gaussian-field form for a closed single-block unit, from the oracle's messages at the
+    sites x_new the GPU drew: factor * sum over positions i = 1..M-1 of
+    max_y alpha_i(y) sum_y W_i(y) G(x_{i+1} - y) / sum_y f_i(y) G(x_{i+1} - y) (the mean of
+    max alpha_i / alpha_i(x_i) given x_{i+1}), plus the end's max alpha_M / alpha_M(x_M)."""
     L, M, N = orc.L, orc.M, orc.N
     g, _ = oracle.g_table(L, orc.t, orc.dtau)
     G = np.fft.fft2(np.outer(g, g))
     xa = int(x_new[sg, p, a])
     _, f = oracle.filter_block(L, M, g, W[sg], a, M, xa, xa, want_f=True)
+    ys = np.arange(N)
+
+    def gcol(x):  # G(x - y) for every y
+        return g[(x % L - ys % L) % L] * g[(x // L - ys // L) % L]
+
     tot = 0.0
-    for i in range(1, M + 1):
-        al = np.real(np.fft.ifft2(np.fft.fft2(f[(a + i - 1) % M].reshape(L, L)) * G)).reshape(-1)
-        tot += al.max() / max(al[int(x_new[sg, p, (a + i) % M])], 1e-300)
-    return tot
+    for i in range(1, M):
+        li = (a + i) % M
+        fi, wi = f[li], W[sg][li]
+        gx = gcol(int(x_new[sg, p, (a + i + 1) % M]))
+        tot += (fi / wi).max() * (wi @ gx) / max(fi @ gx, 1e-300)
+    al = np.real(np.fft.ifft2(np.fft.fft2(f[(a + M - 1) % M].reshape(L, L)) * G)).reshape(-1)
+    return factor * tot + al.max() / max(al[xa], 1e-300)
 
 
 def case_id(case):
@@ -196,7 +207,7 @@ def test_random_combination_matches_oracle(case):
                 if orc.gauss:
                     if perm:
                         continue  # the unit's path crosses worldlines at the permuted boundary
-                    kap = unit_kappa_sum(orc, W, a, sg, p, x) / orc.M
+                    kap = unit_kappa_sum(orc, W, a, sg, p, x, GAUSS_FACTOR[prec]) / orc.M
                 else:
                     kap = unit_kappa(orc, W, a, block, sg, p)
                 if kap < 1e-3 / EPS[prec]:

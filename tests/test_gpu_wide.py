@@ -202,3 +202,25 @@ def test_bf16_checkpoints_against_the_oracle(L, beta, nwl):
     d, f, bad = path_mismatches(x, orc.x, ref["margin"], a, orc.M, 2.0 ** -7, nwl=nwl)
     assert not bad, bad[:3]
     print(f"\nL={L} BF16 checkpoints: {d} draws, {f} first differences ({f / max(1, d):.2e})")
+
+
+@pytest.mark.parametrize("L", [48, 64, 128])
+def test_wide_sweeps_are_reproducible(L):
+    """Two contexts with the same seeds give the same bits: log-weights, paths and fields
+    over two sweeps (the work counter assigns units to CTAs in a different order each run,
+    and every result of a unit depends only on the unit)."""
+    from paper_2510_13866_gb300 import Lattice
+
+    out = []
+    for _ in range(2):
+        lat = Lattice(L, [41, 42], precision="fp32")
+        lat.set_params(1.0, 4.0, 0.3, 0.05, 0.125)
+        lw = [lat.sweep(1, logw=True) for _ in range(2)]
+        out.append((lw, [lat.get_state(c) for c in range(2)]))
+        lat.close()
+    (lw_a, st_a), (lw_b, st_b) = out
+    for k in range(2):
+        for c in range(2):
+            assert np.array_equal(lw_a[k][c], lw_b[k][c]), (k, c)
+    for c in range(2):
+        assert np.array_equal(st_a[c][0], st_b[c][0]) and np.array_equal(st_a[c][1], st_b[c][1])
