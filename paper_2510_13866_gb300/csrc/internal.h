@@ -166,7 +166,8 @@ bool ffbs_supported(int L);
 cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stream);
 cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int slices_per_cta,
                          bool measure, cudaStream_t stream);
-cudaError_t configure_slice();
+cudaError_t configure_slice(int max_L, int S);
+int slice_group(int max_L, int requested);
 void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
 // local link updates: the largest (worldline, slice) count of one colour of a chain, and

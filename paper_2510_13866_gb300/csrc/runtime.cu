@@ -99,7 +99,7 @@ struct hqmc_ctx {
     std::vector<cudaEvent_t> ev;
     bool use_graph = true, persistent = true;
     int wpc = 0;
-    int slices_per_cta = 2;  // Gibbs/measure kernel: slices handled by one CTA
+    int slices_per_cta = 0;  // Gibbs/measure kernel: slices handled by one CTA (0: automatic)
     bool perm_on = false;    // permutation updates at tau = beta in every sweep
     int conv = HQMC_CONV_FFT;  // line convolutions of the FFBS: FFT or periodic stencil
     bool perm_used = false;  // a permutation other than the identity may be in the state
@@ -586,7 +586,11 @@ int prepare(hqmc_ctx *c) {
         rc = occupancy(c, k.L, default_wpc(c, k.L), &bps);
         if (rc) return rc;
     }
-    HQMC_CUDA(c, configure_slice());
+    {
+        int max_L = 0;
+        for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
+        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta)));
+    }
     {
         // permutations start at the identity (and so do their inverses); parity 0 = sign +1
         std::vector<int> ident;
@@ -734,7 +738,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[2], st));
     int max_L = 0;
     for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
-    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, c->slices_per_cta, true, st);
+    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, slice_group(max_L, c->slices_per_cta), true, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
     if (prof) {
         HQMC_CUDA(c, cudaEventRecord(pe[3], st));
@@ -1016,9 +1020,15 @@ int hqmc_set_launch(hqmc_ctx *c, int use_graph, int persistent, int warps_per_ct
 }
 
 int hqmc_set_slice_launch(hqmc_ctx *c, int slices_per_cta) {
-    if (!c || slices_per_cta < 1 || slices_per_cta > 1024) return HQMC_ERR_ARG;
+    if (!c || slices_per_cta < 0 || slices_per_cta > 1024) return HQMC_ERR_ARG;
     c->slices_per_cta = slices_per_cta;
     drop_graph(c);
+    if (c->ready) {
+        // the kernel's shared memory follows the group size (set here, outside any capture)
+        int max_L = 0;
+        for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
+        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta)));
+    }
     return HQMC_OK;
 }
 
@@ -1209,7 +1219,8 @@ int hqmc_local_sweep(hqmc_ctx *c, int n_sweeps) {
             cudaError_t e = launch_local(c->st, c->nchains, max_units, color, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "local launch");
         }
-        cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, c->slices_per_cta, true, c->stream);
+        cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, slice_group(max_L, c->slices_per_cta), true,
+                                     c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
         e = launch_advance(c->st, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");

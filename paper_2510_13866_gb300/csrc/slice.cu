@@ -36,20 +36,23 @@ struct SliceSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-// byte offsets of the slice kernel's shared arrays for lattice size L
-__host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl) {
-    const size_t N = size_t(L) * L;
+// byte offsets of the slice kernel's shared arrays for lattice size L and S slices handled
+// together: per slice the field bits by rows and columns, the slice's m and its row DFT
+__host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl, int S) {
+    const size_t N = size_t(L) * L, K1 = size_t(L) / 2 + 1;
     SliceSmem s{};
     s.rows = 0;
-    s.red = align16(s.rows + 2 * size_t(L) * wpl * 4);
+    s.red = align16(s.rows + size_t(S) * 2 * size_t(L) * wpl * 4);
     s.pp = align16(s.red + 32 * 8);
     s.ms = align16(s.pp + (2 * kPTab + 1) * 8);
-    s.x1 = align16(s.ms + N * 4);
-    s.tw = align16(s.x1 + N * 8);
+    s.x1 = align16(s.ms + size_t(S) * N * 4);
+    s.tw = align16(s.x1 + size_t(S) * K1 * L * 8);
     s.sk = align16(s.tw + size_t(L) * 8);
     s.total = N <= size_t(kSkSmemMaxN) ? align16(s.sk + N * 8) : s.sk;
     return s;
 }
+
+constexpr size_t kSliceSmemBudget = 200 * 1024;
 
 // Gaussian field (U < 0): standard normal by the Box-Muller transform from the two
 // uniforms of j = 2x and 2x+1: z = sqrt(-2 ln(1 - u1)) cos(2 pi u2), in FP64.
@@ -77,42 +80,46 @@ __device__ __forceinline__ void put_gauss(const DevState &st, const ChainDev &cd
 
 }  // namespace
 
-// One CTA per (chain, group of slices).  For every site of a slice:
+// One CTA per (chain, group of S consecutive slices), the slices handled together: every
+// loop below runs over (slice, item) of the whole group, so a small lattice still fills the
+// CTA's threads.  For every site of a slice:
 //   m = n_up - n_dn;  s = +1 iff u < P(s=+1|m) = 1/(1+exp(-2 lambda m))  (FP64 compare),
 // written bit-packed by rows and by columns; the histogram is cleared for the next
 // sweep.  With `measure`, the slice's n, n_up n_dn, m^2 and |m^(k)|^2/N are added to
-// the chain's accumulators (m^ by a direct separable DFT in FP32).
-__global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int slices_per_cta, int measure) {
+// the chain's accumulators (m^ by a direct separable DFT in FP32; each k sums the group's
+// slices in slice order).
+__global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int S, int measure) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int c = blockIdx.y;
     const ChainDev &cd = st.chains[c];
     const int L = cd.L, N = cd.N, M = cd.M, wpl = cd.wpl;
-    const int l_begin = blockIdx.x * slices_per_cta;
+    const int l_begin = blockIdx.x * S;
     if (l_begin >= M) return;
-    const int l_end = min(M, l_begin + slices_per_cta);
+    const int ns = min(M, l_begin + S) - l_begin;  // slices of this CTA
     const uint64_t sweep = *st.sweep;
     const double lam = cd.lam;
     const ChainTab &tb = st.tabs[c];
+    const int K1 = L / 2 + 1;  // kx = 0 .. L/2
 
     const bool do_sk = measure != 0;
     const bool sk_smem = N <= kSkSmemMaxN;
-    const SliceSmem lay = slice_smem_layout(L, wpl);
-    uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
-    uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
+    const SliceSmem lay = slice_smem_layout(L, wpl, S);
+    uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [S][2][L][wpl]
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
     double *pp = reinterpret_cast<double *>(smem_raw + lay.pp);         // P(s=+1 | m), |m| <= kPTab
-    float *ms = reinterpret_cast<float *>(smem_raw + lay.ms);            // [N] m of the slice
-    float2 *x1 = reinterpret_cast<float2 *>(smem_raw + lay.x1);          // [N] row DFT
+    float *ms = reinterpret_cast<float *>(smem_raw + lay.ms);            // [S][N] m of the slices
+    float2 *x1 = reinterpret_cast<float2 *>(smem_raw + lay.x1);          // [S][L][K1] row DFTs
     float2 *tw = reinterpret_cast<float2 *>(smem_raw + lay.tw);          // [L] e^{-2 pi i j / L}
     double *skacc = reinterpret_cast<double *>(smem_raw + lay.sk);       // [N]
+    const int bits = 2 * L * wpl;  // words of one slice's rows and columns
 
-    for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+    for (int k = threadIdx.x; k < ns * bits; k += blockDim.x) rows[k] = 0u;
     for (int k = threadIdx.x; k < 2 * kPTab + 1; k += blockDim.x) pp[k] = tb.pplus[k];
     if (do_sk) {
         for (int j = threadIdx.x; j < L; j += blockDim.x) {
-            float s, co;
-            sincospif(2.0f * float(j) / float(L), &s, &co);
-            tw[j] = make_float2(co, -s);
+            float sn, co;
+            sincospif(2.0f * float(j) / float(L), &sn, &co);
+            tw[j] = make_float2(co, -sn);
         }
         if (sk_smem)
             for (int k = threadIdx.x; k < N; k += blockDim.x) skacc[k] = 0.0;
@@ -125,44 +132,48 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
     uint32_t *srow_g = st.sbits + cd.s_off;
     uint32_t *scol_g = srow_g + (long long)M * L * wpl;
 
-    for (int l = l_begin; l < l_end; ++l) {
-        int *hu = hu_base + (long long)l * N;
-        int *hd = hd_base + (long long)l * N;
-        if (cd.gauss) {
-            // Gaussian field: sigma ~ N(a (n_up + n_dn - 1/2), 1), uniforms j = 2x, 2x+1
-            const int npairs = (N + 1) >> 1;
-            for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
-                const u64x4 w4 = philox4x64_10((uint64_t)pr, (uint64_t)l, 1, sweep, cd.seed, 0);
+    if (cd.gauss) {
+        // Gaussian field: sigma ~ N(a (n_up + n_dn - 1/2), 1), uniforms j = 2x, 2x+1
+        const int npairs = (N + 1) >> 1;
+        for (int it = threadIdx.x; it < ns * npairs; it += blockDim.x) {
+            const int sl = it / npairs, pr = it - sl * npairs, l = l_begin + sl;
+            int *hu = hu_base + (long long)l * N;
+            int *hd = hd_base + (long long)l * N;
+            const u64x4 w4 = philox4x64_10((uint64_t)pr, (uint64_t)l, 1, sweep, cd.seed, 0);
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int x = 2 * pr + j;
-                    if (x >= N) break;
-                    const int nu = hu[x], nd = hd[x];
-                    hu[x] = 0;
-                    hd[x] = 0;
-                    const int m = nu - nd;
-                    put_gauss(st, cd, l, x, cd.gcoup * (double(nu + nd) - 0.5) + box_muller(w4.v[2 * j], w4.v[2 * j + 1]));
-                    if (measure) {
-                        n_acc += (unsigned long long)(nu + nd);
-                        d_acc += (unsigned long long)(nu * nd);
-                        m2_acc += (unsigned long long)(m * m);
-                        if (do_sk) ms[x] = float(m);
-                    }
+            for (int j = 0; j < 2; ++j) {
+                const int x = 2 * pr + j;
+                if (x >= N) break;
+                const int nu = hu[x], nd = hd[x];
+                hu[x] = 0;
+                hd[x] = 0;
+                const int m = nu - nd;
+                put_gauss(st, cd, l, x, cd.gcoup * (double(nu + nd) - 0.5) + box_muller(w4.v[2 * j], w4.v[2 * j + 1]));
+                if (measure) {
+                    n_acc += (unsigned long long)(nu + nd);
+                    d_acc += (unsigned long long)(nu * nd);
+                    m2_acc += (unsigned long long)(m * m);
+                    if (do_sk) ms[sl * N + x] = float(m);
                 }
             }
         }
-        const int nquads = cd.gauss ? 0 : (N + 3) >> 2;
-        // whole quads of 16-byte aligned counts move as one vector load and one store
-        const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(hu) | reinterpret_cast<uintptr_t>(hd)) & 15) == 0;
-        for (int qd = threadIdx.x; qd < nquads; qd += blockDim.x) {
+    } else {
+        const int nquads = (N + 3) >> 2;
+        for (int it = threadIdx.x; it < ns * nquads; it += blockDim.x) {
+            const int sl = it / nquads, qd = it - sl * nquads, l = l_begin + sl;
+            int *hu = hu_base + (long long)l * N;
+            int *hd = hd_base + (long long)l * N;
+            uint32_t *rw = rows + sl * bits, *cl = rw + L * wpl;
             const u64x4 w4 = philox4x64_10((uint64_t)qd, (uint64_t)l, 1, sweep, cd.seed, 0);
+            // whole quads of 16-byte aligned counts move as one vector load and one store
+            const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(hu) | reinterpret_cast<uintptr_t>(hd)) & 15) == 0;
             int nuq[4], ndq[4];
             if (vec) {
-                const int4 a = reinterpret_cast<const int4 *>(hu)[qd], b = reinterpret_cast<const int4 *>(hd)[qd];
+                const int4 a4 = reinterpret_cast<const int4 *>(hu)[qd], b4 = reinterpret_cast<const int4 *>(hd)[qd];
                 reinterpret_cast<int4 *>(hu)[qd] = make_int4(0, 0, 0, 0);
                 reinterpret_cast<int4 *>(hd)[qd] = make_int4(0, 0, 0, 0);
-                nuq[0] = a.x; nuq[1] = a.y; nuq[2] = a.z; nuq[3] = a.w;
-                ndq[0] = b.x; ndq[1] = b.y; ndq[2] = b.z; ndq[3] = b.w;
+                nuq[0] = a4.x; nuq[1] = a4.y; nuq[2] = a4.z; nuq[3] = a4.w;
+                ndq[0] = b4.x; ndq[1] = b4.y; ndq[2] = b4.z; ndq[3] = b4.w;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -186,67 +197,74 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
                 const bool up = u53(w4.v[j]) < pplus;
                 const int ix = x % L, iy = x / L;
                 if (up) {
-                    atomicOr(&rows[iy * wpl + (ix >> 5)], 1u << (ix & 31));
-                    atomicOr(&cols[ix * wpl + (iy >> 5)], 1u << (iy & 31));
+                    atomicOr(&rw[iy * wpl + (ix >> 5)], 1u << (ix & 31));
+                    atomicOr(&cl[ix * wpl + (iy >> 5)], 1u << (iy & 31));
                 }
                 if (measure) {
                     n_acc += (unsigned long long)(nu + nd);
                     d_acc += (unsigned long long)(nu * nd);
                     m2_acc += (unsigned long long)(m * m);
-                    if (do_sk) ms[x] = float(m);
+                    if (do_sk) ms[sl * N + x] = float(m);
                 }
             }
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < (cd.gauss ? 0 : L * wpl); k += blockDim.x) {
-            srow_g[(long long)l * L * wpl + k] = rows[k];
-            scol_g[(long long)l * L * wpl + k] = cols[k];
+    }
+    __syncthreads();
+    if (!cd.gauss) {
+        for (int k = threadIdx.x; k < ns * L * wpl; k += blockDim.x) {
+            const int sl = k / (L * wpl), kk = k - sl * (L * wpl);
+            const long long off = (long long)(l_begin + sl) * L * wpl + kk;
+            srow_g[off] = rows[sl * bits + kk];
+            scol_g[off] = rows[sl * bits + L * wpl + kk];
         }
-        // S(k) of a real field: m^(-k) = conj(m^(k)), so only kx = 0..L/2 is transformed and
-        // |m^(L - kx, L - ky)|^2 = |m^(kx, ky)|^2 fills the other half
-        const int K1 = L / 2 + 1;  // kx = 0 .. L/2
-        if (do_sk) {
-            // x1[iy][kx] = sum_ix m[iy][ix] e^{-2 pi i kx ix / L}
-            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
-                const int kx = o % K1, iy = o / K1;
-                float re = 0.f, im = 0.f;
-                int ph = 0;
-                for (int ix = 0; ix < L; ++ix) {
-                    const float mv = ms[iy * L + ix];
-                    re += mv * tw[ph].x;
-                    im += mv * tw[ph].y;
-                    ph += kx;
-                    if (ph >= L) ph -= L;
-                }
-                x1[o] = make_float2(re, im);
+    }
+    // S(k) of a real field: m^(-k) = conj(m^(k)), so only kx = 0..L/2 is transformed and
+    // |m^(L - kx, L - ky)|^2 = |m^(kx, ky)|^2 fills the other half
+    if (do_sk) {
+        // x1[sl][iy][kx] = sum_ix m[sl][iy][ix] e^{-2 pi i kx ix / L}
+        for (int o = threadIdx.x; o < ns * K1 * L; o += blockDim.x) {
+            const int sl = o / (K1 * L), r = o - sl * (K1 * L);
+            const int kx = r % K1, iy = r / K1;
+            const float *msl = ms + sl * N + iy * L;
+            float re = 0.f, im = 0.f;
+            int ph = 0;
+            for (int ix = 0; ix < L; ++ix) {
+                const float mv = msl[ix];
+                re += mv * tw[ph].x;
+                im += mv * tw[ph].y;
+                ph += kx;
+                if (ph >= L) ph -= L;
             }
+            x1[o] = make_float2(re, im);
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
-        if (do_sk) {
-            // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N
-            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
-                const int kx = o % K1, ky = o / K1;
+        // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N, the group's
+        // slices summed in slice order by the thread that owns k
+        for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
+            const int kx = o % K1, ky = o / K1;
+            double v = 0.0;
+            for (int sl = 0; sl < ns; ++sl) {
+                const float2 *xs = x1 + sl * (K1 * L);
                 float re = 0.f, im = 0.f;
                 int ph = 0;
                 for (int iy = 0; iy < L; ++iy) {
-                    const float2 a = x1[iy * K1 + kx], w = tw[ph];
+                    const float2 a = xs[iy * K1 + kx], w = tw[ph];
                     re += a.x * w.x - a.y * w.y;
                     im += a.x * w.y + a.y * w.x;
                     ph += ky;
                     if (ph >= L) ph -= L;
                 }
-                const double v = double(re * re + im * im) / double(N);
-                const int k = ky * L + kx;
-                const bool mirror = kx > 0 && 2 * kx < L;
-                const int km = (ky == 0 ? 0 : L - ky) * L + (L - kx);
-                if (sk_smem) {
-                    skacc[k] += v;
-                    if (mirror) skacc[km] += v;
-                } else {
-                    atomicAdd(&st.sk[cd.meas_off + k], v * chain_sign(st, c));
-                    if (mirror) atomicAdd(&st.sk[cd.meas_off + km], v * chain_sign(st, c));
-                }
+                v += double(re * re + im * im) / double(N);
+            }
+            const int k = ky * L + kx;
+            const bool mirror = kx > 0 && 2 * kx < L;
+            const int km = (ky == 0 ? 0 : L - ky) * L + (L - kx);
+            if (sk_smem) {
+                skacc[k] += v;
+                if (mirror) skacc[km] += v;
+            } else {
+                atomicAdd(&st.sk[cd.meas_off + k], v * chain_sign(st, c));
+                if (mirror) atomicAdd(&st.sk[cd.meas_off + km], v * chain_sign(st, c));
             }
         }
         __syncthreads();
@@ -269,25 +287,26 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
     }
 }
 
-static size_t slice_smem_max() {
-    // the layout depends on L; size it for the largest layout any supported lattice needs
-    size_t sm = 0;
-    for (int L = 2; L <= kMaxL; ++L) {
-        const size_t t = slice_smem_layout(L, (L + 31) / 32).total;
-        sm = t > sm ? t : sm;
-    }
-    return sm;
+// slices handled together by one CTA for the context's largest lattice: `requested` (> 0)
+// or, with 0, enough to give every thread about four sites (1024 per CTA, at least 2),
+// capped by the shared memory the group's arrays need
+int slice_group(int max_L, int requested) {
+    const int wpl = (max_L + 31) / 32;
+    int S = requested > 0 ? requested : std::max(2, std::min(16, 1024 / (max_L * max_L)));
+    while (S > 1 && slice_smem_layout(max_L, wpl, S).total > kSliceSmemBudget) --S;
+    return S;
 }
 
-cudaError_t configure_slice() {
-    return cudaFuncSetAttribute(slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slice_smem_max()));
+cudaError_t configure_slice(int max_L, int S) {
+    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32, S).total;
+    return cudaFuncSetAttribute(slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
 }
 
-cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int slices_per_cta, bool measure,
+cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int S, bool measure,
                          cudaStream_t stream) {
-    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32).total;
-    dim3 grid((max_M + slices_per_cta - 1) / slices_per_cta, nchains);
-    slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, slices_per_cta, measure ? 1 : 0);
+    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32, S).total;
+    dim3 grid((max_M + S - 1) / S, nchains);
+    slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, S, measure ? 1 : 0);
     return cudaGetLastError();
 }
 
