@@ -168,12 +168,14 @@ int hqmc_set_stream(hqmc_ctx *ctx, void *stream);
  * the context out as described at hqmc_set_class_launch.  Errors: HQMC_ERR_ARG. */
 int hqmc_set_launch(hqmc_ctx *ctx, int use_graph, int persistent, int warps_per_cta);
 
-/* Slices of one chain handled together by one CTA of the Gibbs/measure kernel: every loop
- * of the kernel runs over (slice, site) of the group, so small lattices still fill the CTA.
- * 0 (the default) chooses about 1024 sites per CTA for the context's largest lattice, at
- * least 2 slices (16 at L = 8, 4 at L = 16, 2 from L = 24 on); any value is capped by the
- * shared memory the group needs.  The fields, paths and integer sums do not depend on it;
- * S(k) may differ by FP64 rounding.  Errors: HQMC_ERR_ARG (outside 0..1024). */
+/* Slices of one chain handled by one CTA of the Gibbs/measure kernel.  Up to L = 12 (the
+ * context's largest lattice) the CTA handles its slices together, every loop running over
+ * (slice, site) of the group, so a small lattice still fills the CTA; beyond, it handles them
+ * one after another.  0 (the default) picks what measured fastest on GB300: 16 slices up to
+ * L = 12 (fewer when the grid would hold under two CTAs per SM), then 4 up to L = 16, 2 up
+ * to L = 48 and 1 above.  The grouped form caps the value by the shared memory the group
+ * needs.  The fields, paths and integer sums do not depend
+ * on it; S(k) may differ by FP64 rounding.  Errors: HQMC_ERR_ARG (outside 0..1024). */
 int hqmc_set_slice_launch(hqmc_ctx *ctx, int slices_per_cta);
 
 /* Warps per CTA of the FFBS kernel for the chains of lattice size L only (0 = the

@@ -167,7 +167,7 @@ cudaError_t launch_init_state(const DevState &st, int nchains, cudaStream_t stre
 cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int slices_per_cta,
                          bool measure, cudaStream_t stream);
 cudaError_t configure_slice(int max_L, int S);
-int slice_group(int max_L, int requested);
+int slice_group(int max_L, int requested, long long work_slices, int num_sms);
 void host_chain_table(int L, double t, double U, double dtau, ChainTab &tb, double *lam);
 cudaError_t launch_advance(const DevState &st, cudaStream_t stream);
 // local link updates: the largest (worldline, slice) count of one colour of a chain, and

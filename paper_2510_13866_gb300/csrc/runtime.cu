@@ -315,6 +315,13 @@ int occupancy(hqmc_ctx *c, int L, int wpc, int *blocks) {
     return HQMC_OK;
 }
 
+// chains x the longest M: the Gibbs/measure kernel's work in slices
+long long slice_work(const hqmc_ctx *c) {
+    int max_M = 0;
+    for (auto &d : c->cdev) max_M = std::max(max_M, d.M);
+    return (long long)c->nchains * max_M;
+}
+
 int default_wpc(hqmc_ctx *c, int L) {
     for (auto &kv : c->class_wpc)
         if (kv.first == L && kv.second > 0) return kv.second;
@@ -589,7 +596,7 @@ int prepare(hqmc_ctx *c) {
     {
         int max_L = 0;
         for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
-        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta)));
+        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta, slice_work(c), c->num_sms)));
     }
     {
         // permutations start at the identity (and so do their inverses); parity 0 = sign +1
@@ -738,7 +745,8 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[2], st));
     int max_L = 0;
     for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
-    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, slice_group(max_L, c->slices_per_cta), true, st);
+    const int sgroup = slice_group(max_L, c->slices_per_cta, slice_work(c), c->num_sms);
+    cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, sgroup, true, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
     if (prof) {
         HQMC_CUDA(c, cudaEventRecord(pe[3], st));
@@ -1027,7 +1035,7 @@ int hqmc_set_slice_launch(hqmc_ctx *c, int slices_per_cta) {
         // the kernel's shared memory follows the group size (set here, outside any capture)
         int max_L = 0;
         for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
-        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta)));
+        HQMC_CUDA(c, configure_slice(max_L, slice_group(max_L, c->slices_per_cta, slice_work(c), c->num_sms)));
     }
     return HQMC_OK;
 }
@@ -1219,7 +1227,7 @@ int hqmc_local_sweep(hqmc_ctx *c, int n_sweeps) {
             cudaError_t e = launch_local(c->st, c->nchains, max_units, color, c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "local launch");
         }
-        cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, slice_group(max_L, c->slices_per_cta), true,
+        cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, slice_group(max_L, c->slices_per_cta, slice_work(c), c->num_sms), true,
                                      c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
         e = launch_advance(c->st, c->stream);

@@ -53,6 +53,7 @@ __host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl, int S) {
 }
 
 constexpr size_t kSliceSmemBudget = 200 * 1024;
+constexpr int kGroupMaxL = 12;  // the grouped form up to this lattice size
 
 // Gaussian field (U < 0): standard normal by the Box-Muller transform from the two
 // uniforms of j = 2x and 2x+1: z = sqrt(-2 ln(1 - u1)) cos(2 pi u2), in FP64.
@@ -80,15 +81,209 @@ __device__ __forceinline__ void put_gauss(const DevState &st, const ChainDev &cd
 
 }  // namespace
 
-// One CTA per (chain, group of S consecutive slices), the slices handled together: every
-// loop below runs over (slice, item) of the whole group, so a small lattice still fills the
-// CTA's threads.  For every site of a slice:
+// Sequential form (lattices above kGroupMaxL): one CTA per (chain, group of
+// slices_per_cta slices), the slices one after another through the same shared arrays.
+// For every site of a slice:
+//   m = n_up - n_dn;  s = +1 iff u < P(s=+1|m) = 1/(1+exp(-2 lambda m))  (FP64 compare),
+// written bit-packed by rows and by columns; the histogram is cleared for the next
+// sweep.  With `measure`, the slice's n, n_up n_dn, m^2 and |m^(k)|^2/N are added to
+// the chain's accumulators (m^ by a direct separable DFT in FP32).
+__global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int slices_per_cta, int measure) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = blockIdx.y;
+    const ChainDev &cd = st.chains[c];
+    const int L = cd.L, N = cd.N, M = cd.M, wpl = cd.wpl;
+    const int l_begin = blockIdx.x * slices_per_cta;
+    if (l_begin >= M) return;
+    const int l_end = min(M, l_begin + slices_per_cta);
+    const uint64_t sweep = *st.sweep;
+    const double lam = cd.lam;
+    const ChainTab &tb = st.tabs[c];
+
+    const bool do_sk = measure != 0;
+    const bool sk_smem = N <= kSkSmemMaxN;
+    const SliceSmem lay = slice_smem_layout(L, wpl, 1);
+    uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
+    uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
+    double *pp = reinterpret_cast<double *>(smem_raw + lay.pp);         // P(s=+1 | m), |m| <= kPTab
+    float *ms = reinterpret_cast<float *>(smem_raw + lay.ms);            // [N] m of the slice
+    float2 *x1 = reinterpret_cast<float2 *>(smem_raw + lay.x1);          // [N] row DFT
+    float2 *tw = reinterpret_cast<float2 *>(smem_raw + lay.tw);          // [L] e^{-2 pi i j / L}
+    double *skacc = reinterpret_cast<double *>(smem_raw + lay.sk);       // [N]
+
+    for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+    for (int k = threadIdx.x; k < 2 * kPTab + 1; k += blockDim.x) pp[k] = tb.pplus[k];
+    if (do_sk) {
+        for (int j = threadIdx.x; j < L; j += blockDim.x) {
+            float s, co;
+            sincospif(2.0f * float(j) / float(L), &s, &co);
+            tw[j] = make_float2(co, -s);
+        }
+        if (sk_smem)
+            for (int k = threadIdx.x; k < N; k += blockDim.x) skacc[k] = 0.0;
+    }
+    __syncthreads();
+
+    unsigned long long n_acc = 0, d_acc = 0, m2_acc = 0;
+    int *hu_base = st.hist + cd.h_off;
+    int *hd_base = hu_base + (long long)M * N;
+    uint32_t *srow_g = st.sbits + cd.s_off;
+    uint32_t *scol_g = srow_g + (long long)M * L * wpl;
+
+    for (int l = l_begin; l < l_end; ++l) {
+        int *hu = hu_base + (long long)l * N;
+        int *hd = hd_base + (long long)l * N;
+        if (cd.gauss) {
+            // Gaussian field: sigma ~ N(a (n_up + n_dn - 1/2), 1), uniforms j = 2x, 2x+1
+            const int npairs = (N + 1) >> 1;
+            for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+                const u64x4 w4 = philox4x64_10((uint64_t)pr, (uint64_t)l, 1, sweep, cd.seed, 0);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int x = 2 * pr + j;
+                    if (x >= N) break;
+                    const int nu = hu[x], nd = hd[x];
+                    hu[x] = 0;
+                    hd[x] = 0;
+                    const int m = nu - nd;
+                    put_gauss(st, cd, l, x, cd.gcoup * (double(nu + nd) - 0.5) + box_muller(w4.v[2 * j], w4.v[2 * j + 1]));
+                    if (measure) {
+                        n_acc += (unsigned long long)(nu + nd);
+                        d_acc += (unsigned long long)(nu * nd);
+                        m2_acc += (unsigned long long)(m * m);
+                        if (do_sk) ms[x] = float(m);
+                    }
+                }
+            }
+        }
+        const int nquads = cd.gauss ? 0 : (N + 3) >> 2;
+        // whole quads of 16-byte aligned counts move as one vector load and one store
+        const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(hu) | reinterpret_cast<uintptr_t>(hd)) & 15) == 0;
+        for (int qd = threadIdx.x; qd < nquads; qd += blockDim.x) {
+            const u64x4 w4 = philox4x64_10((uint64_t)qd, (uint64_t)l, 1, sweep, cd.seed, 0);
+            int nuq[4], ndq[4];
+            if (vec) {
+                const int4 a = reinterpret_cast<const int4 *>(hu)[qd], b = reinterpret_cast<const int4 *>(hd)[qd];
+                reinterpret_cast<int4 *>(hu)[qd] = make_int4(0, 0, 0, 0);
+                reinterpret_cast<int4 *>(hd)[qd] = make_int4(0, 0, 0, 0);
+                nuq[0] = a.x; nuq[1] = a.y; nuq[2] = a.z; nuq[3] = a.w;
+                ndq[0] = b.x; ndq[1] = b.y; ndq[2] = b.z; ndq[3] = b.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int x = 4 * qd + j;
+                    nuq[j] = x < N ? hu[x] : 0;
+                    ndq[j] = x < N ? hd[x] : 0;
+                    if (x < N) {
+                        hu[x] = 0;
+                        hd[x] = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = 4 * qd + j;
+                if (x >= N) break;
+                const int nu = nuq[j], nd = ndq[j];
+                const int m = nu - nd;
+                const double pplus = (m >= -kPTab && m <= kPTab) ? pp[m + kPTab]
+                                                                  : 1.0 / (1.0 + exp(-2.0 * lam * m));
+                const bool up = u53(w4.v[j]) < pplus;
+                const int ix = x % L, iy = x / L;
+                if (up) {
+                    atomicOr(&rows[iy * wpl + (ix >> 5)], 1u << (ix & 31));
+                    atomicOr(&cols[ix * wpl + (iy >> 5)], 1u << (iy & 31));
+                }
+                if (measure) {
+                    n_acc += (unsigned long long)(nu + nd);
+                    d_acc += (unsigned long long)(nu * nd);
+                    m2_acc += (unsigned long long)(m * m);
+                    if (do_sk) ms[x] = float(m);
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < (cd.gauss ? 0 : L * wpl); k += blockDim.x) {
+            srow_g[(long long)l * L * wpl + k] = rows[k];
+            scol_g[(long long)l * L * wpl + k] = cols[k];
+        }
+        // S(k) of a real field: m^(-k) = conj(m^(k)), so only kx = 0..L/2 is transformed and
+        // |m^(L - kx, L - ky)|^2 = |m^(kx, ky)|^2 fills the other half
+        const int K1 = L / 2 + 1;  // kx = 0 .. L/2
+        if (do_sk) {
+            // x1[iy][kx] = sum_ix m[iy][ix] e^{-2 pi i kx ix / L}
+            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
+                const int kx = o % K1, iy = o / K1;
+                float re = 0.f, im = 0.f;
+                int ph = 0;
+                for (int ix = 0; ix < L; ++ix) {
+                    const float mv = ms[iy * L + ix];
+                    re += mv * tw[ph].x;
+                    im += mv * tw[ph].y;
+                    ph += kx;
+                    if (ph >= L) ph -= L;
+                }
+                x1[o] = make_float2(re, im);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * L * wpl; k += blockDim.x) rows[k] = 0u;
+        if (do_sk) {
+            // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N
+            for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
+                const int kx = o % K1, ky = o / K1;
+                float re = 0.f, im = 0.f;
+                int ph = 0;
+                for (int iy = 0; iy < L; ++iy) {
+                    const float2 a = x1[iy * K1 + kx], w = tw[ph];
+                    re += a.x * w.x - a.y * w.y;
+                    im += a.x * w.y + a.y * w.x;
+                    ph += ky;
+                    if (ph >= L) ph -= L;
+                }
+                const double v = double(re * re + im * im) / double(N);
+                const int k = ky * L + kx;
+                const bool mirror = kx > 0 && 2 * kx < L;
+                const int km = (ky == 0 ? 0 : L - ky) * L + (L - kx);
+                if (sk_smem) {
+                    skacc[k] += v;
+                    if (mirror) skacc[km] += v;
+                } else {
+                    atomicAdd(&st.sk[cd.meas_off + k], v * chain_sign(st, c));
+                    if (mirror) atomicAdd(&st.sk[cd.meas_off + km], v * chain_sign(st, c));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (measure) {
+        // sums weighted by the sweep's sign sgn(P_up) sgn(P_dn) (Eq. reweight; +1 without
+        // permutations), negative contributions in two's complement
+        const int sgn = chain_sign(st, c);
+        auto wsum = [&](unsigned long long v) { return sgn > 0 ? v : 0ull - v; };
+        MeasAcc &acc = st.meas[c];
+        block_add_u64(wsum(n_acc), &acc.n_sum, red);
+        block_add_u64(wsum(d_acc), &acc.d_sum, red);
+        block_add_u64(wsum(m2_acc), &acc.m2_sum, red);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd(&acc.samples, 1ull);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&acc.sign_sum), (unsigned long long)(long long)sgn);
+        }
+        if (do_sk && sk_smem)
+            for (int k = threadIdx.x; k < N; k += blockDim.x) atomicAdd(&st.sk[cd.meas_off + k], skacc[k] * sgn);
+    }
+}
+
+// Grouped form (lattices up to kGroupMaxL): one CTA per (chain, group of S consecutive
+// slices), the slices handled together: every loop below runs over (slice, item) of the
+// whole group, so a small lattice still fills the CTA's threads.  For every site of a slice:
 //   m = n_up - n_dn;  s = +1 iff u < P(s=+1|m) = 1/(1+exp(-2 lambda m))  (FP64 compare),
 // written bit-packed by rows and by columns; the histogram is cleared for the next
 // sweep.  With `measure`, the slice's n, n_up n_dn, m^2 and |m^(k)|^2/N are added to
 // the chain's accumulators (m^ by a direct separable DFT in FP32; each k sums the group's
 // slices in slice order).
-__global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int S, int measure) {
+__global__ void __launch_bounds__(kSliceThreads) slice_group_kernel(DevState st, int S, int measure) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int c = blockIdx.y;
     const ChainDev &cd = st.chains[c];
@@ -287,26 +482,40 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int S
     }
 }
 
-// slices handled together by one CTA for the context's largest lattice: `requested` (> 0)
-// or, with 0, enough to give every thread about four sites (1024 per CTA, at least 2),
-// capped by the shared memory the group's arrays need
-int slice_group(int max_L, int requested) {
+// Slices per CTA for the context's largest lattice: `requested` (> 0), or with 0 the fastest
+// measured on GB300 (Gibbs/measure ms per sweep): up to L = 12 the grouped form with 16
+// slices (L = 8, M = 1024, 32 chains: 0.138 against 0.244 for the sequential form's best);
+// beyond, the sequential form with 4 slices at L <= 16, 2 at L <= 48 and 1 above (0.182
+// ms at L = 16, 0.178 at L = 32, 0.526 at L = 64).  Any value is capped by shared memory.
+// The automatic grouped choice also leaves at least two CTAs per SM (work_slices = chains x
+// the longest M): one L = 8 chain of M = 1024 takes 3 slices per CTA, not 16.
+int slice_group(int max_L, int requested, long long work_slices, int num_sms) {
     const int wpl = (max_L + 31) / 32;
-    int S = requested > 0 ? requested : std::max(2, std::min(16, 1024 / (max_L * max_L)));
-    while (S > 1 && slice_smem_layout(max_L, wpl, S).total > kSliceSmemBudget) --S;
+    const bool grouped = max_L <= kGroupMaxL;
+    int S = requested > 0 ? requested : grouped ? 16 : max_L <= 16 ? 4 : max_L <= 48 ? 2 : 1;
+    if (requested <= 0 && grouped && num_sms > 0)
+        S = int(std::max(1LL, std::min<long long>(S, work_slices / (2LL * num_sms))));
+    if (grouped)
+        while (S > 1 && slice_smem_layout(max_L, wpl, S).total > kSliceSmemBudget) --S;
     return S;
 }
 
+static size_t slice_smem(int max_L, int S) {
+    const int wpl = (max_L + 31) / 32;
+    return slice_smem_layout(max_L, wpl, max_L <= kGroupMaxL ? S : 1).total;
+}
+
 cudaError_t configure_slice(int max_L, int S) {
-    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32, S).total;
-    return cudaFuncSetAttribute(slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    auto k = max_L <= kGroupMaxL ? slice_group_kernel : slice_kernel;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(slice_smem(max_L, S)));
 }
 
 cudaError_t launch_slice(const DevState &st, int nchains, int max_M, int max_L, int S, bool measure,
                          cudaStream_t stream) {
-    const size_t sm = slice_smem_layout(max_L, (max_L + 31) / 32, S).total;
+    const size_t sm = slice_smem(max_L, S);
     dim3 grid((max_M + S - 1) / S, nchains);
-    slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, S, measure ? 1 : 0);
+    if (max_L <= kGroupMaxL) slice_group_kernel<<<grid, kSliceThreads, sm, stream>>>(st, S, measure ? 1 : 0);
+    else slice_kernel<<<grid, kSliceThreads, sm, stream>>>(st, S, measure ? 1 : 0);
     return cudaGetLastError();
 }
 
