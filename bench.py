@@ -388,6 +388,8 @@ def main():
                     help="permutation updates at tau = beta in every sweep (sign-reweighted observables)")
     ap.add_argument("--block", type=int, default=0,
                     help="FFBS block length B (0: the closed loop from the anchor, the default)")
+    ap.add_argument("--slice-group", type=int, default=0,
+                    help="slices per CTA of the Gibbs/measure kernel (0: the library's choice, the default)")
     ap.add_argument("--beta", type=float, default=None,
                     help="beta of the L64/L128 workloads (default 8; smaller only for profiling captures), "
                          "or of L32 in place of its beta = 4")
@@ -442,6 +444,8 @@ def main():
                 lt.set_params(*p, chain=c)
         if args.block:
             lt.set_block(args.block)
+        if args.slice_group:
+            lt.set_slice_launch(args.slice_group)
         if args.perm:
             lt.set_permutations(True)
         if args.conv != "fft":
