@@ -31,14 +31,15 @@ __device__ void block_add_u64(unsigned long long v, unsigned long long *dst, uns
 }
 
 struct SliceSmem {
-    size_t rows, red, pp, ms, x1, tw, sk, total;
+    size_t rows, red, pp, ms, x1, vb, tw, sk, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 // byte offsets of the slice kernel's shared arrays for lattice size L and S slices handled
-// together: per slice the field bits by rows and columns, the slice's m and its row DFT
-__host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl, int S) {
+// together: per slice the field bits by rows and columns, the slice's m and its row DFT,
+// and (grouped form) its |m^(k)|^2 before the sum over the group's slices
+__host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl, int S, bool grouped) {
     const size_t N = size_t(L) * L, K1 = size_t(L) / 2 + 1;
     SliceSmem s{};
     s.rows = 0;
@@ -46,7 +47,8 @@ __host__ __device__ inline SliceSmem slice_smem_layout(int L, int wpl, int S) {
     s.pp = align16(s.red + 32 * 8);
     s.ms = align16(s.pp + (2 * kPTab + 1) * 8);
     s.x1 = align16(s.ms + size_t(S) * N * 4);
-    s.tw = align16(s.x1 + size_t(S) * K1 * L * 8);
+    s.vb = align16(s.x1 + size_t(S) * K1 * L * 8);
+    s.tw = align16(s.vb + (grouped ? size_t(S) * K1 * L * 8 : 0));
     s.sk = align16(s.tw + size_t(L) * 8);
     s.total = N <= size_t(kSkSmemMaxN) ? align16(s.sk + N * 8) : s.sk;
     return s;
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kSliceThreads) slice_kernel(DevState st, int s
 
     const bool do_sk = measure != 0;
     const bool sk_smem = N <= kSkSmemMaxN;
-    const SliceSmem lay = slice_smem_layout(L, wpl, 1);
+    const SliceSmem lay = slice_smem_layout(L, wpl, 1, false);
     uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [L][wpl]
     uint32_t *cols = rows + L * wpl;                                     // [L][wpl]
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kSliceThreads) slice_group_kernel(DevState st,
 
     const bool do_sk = measure != 0;
     const bool sk_smem = N <= kSkSmemMaxN;
-    const SliceSmem lay = slice_smem_layout(L, wpl, S);
+    const SliceSmem lay = slice_smem_layout(L, wpl, S, true);
     uint32_t *rows = reinterpret_cast<uint32_t *>(smem_raw + lay.rows);  // [S][2][L][wpl]
     unsigned long long *red = reinterpret_cast<unsigned long long *>(smem_raw + lay.red);
     double *pp = reinterpret_cast<double *>(smem_raw + lay.pp);         // P(s=+1 | m), |m| <= kPTab
@@ -433,24 +435,30 @@ __global__ void __launch_bounds__(kSliceThreads) slice_group_kernel(DevState st,
             x1[o] = make_float2(re, im);
         }
         __syncthreads();
-        // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L};  S += |m^|^2 / N, the group's
-        // slices summed in slice order by the thread that owns k
+        // m^[ky][kx] = sum_iy x1[iy][kx] e^{-2 pi i ky iy / L} for every (slice, k) of the
+        // group, |m^|^2 / N into vb; then S += the group's slices summed in slice order by the
+        // thread that owns k
+        double *vb = reinterpret_cast<double *>(smem_raw + lay.vb);
+        for (int o = threadIdx.x; o < ns * K1 * L; o += blockDim.x) {
+            const int sl = o / (K1 * L), r = o - sl * (K1 * L);
+            const int kx = r % K1, ky = r / K1;
+            const float2 *xs = x1 + sl * (K1 * L);
+            float re = 0.f, im = 0.f;
+            int ph = 0;
+            for (int iy = 0; iy < L; ++iy) {
+                const float2 a = xs[iy * K1 + kx], w = tw[ph];
+                re += a.x * w.x - a.y * w.y;
+                im += a.x * w.y + a.y * w.x;
+                ph += ky;
+                if (ph >= L) ph -= L;
+            }
+            vb[o] = double(re * re + im * im) / double(N);
+        }
+        __syncthreads();
         for (int o = threadIdx.x; o < K1 * L; o += blockDim.x) {
             const int kx = o % K1, ky = o / K1;
             double v = 0.0;
-            for (int sl = 0; sl < ns; ++sl) {
-                const float2 *xs = x1 + sl * (K1 * L);
-                float re = 0.f, im = 0.f;
-                int ph = 0;
-                for (int iy = 0; iy < L; ++iy) {
-                    const float2 a = xs[iy * K1 + kx], w = tw[ph];
-                    re += a.x * w.x - a.y * w.y;
-                    im += a.x * w.y + a.y * w.x;
-                    ph += ky;
-                    if (ph >= L) ph -= L;
-                }
-                v += double(re * re + im * im) / double(N);
-            }
+            for (int sl = 0; sl < ns; ++sl) v += vb[sl * (K1 * L) + o];
             const int k = ky * L + kx;
             const bool mirror = kx > 0 && 2 * kx < L;
             const int km = (ky == 0 ? 0 : L - ky) * L + (L - kx);
@@ -496,13 +504,14 @@ int slice_group(int max_L, int requested, long long work_slices, int num_sms) {
     if (requested <= 0 && grouped && num_sms > 0)
         S = int(std::max(1LL, std::min<long long>(S, work_slices / (2LL * num_sms))));
     if (grouped)
-        while (S > 1 && slice_smem_layout(max_L, wpl, S).total > kSliceSmemBudget) --S;
+        while (S > 1 && slice_smem_layout(max_L, wpl, S, true).total > kSliceSmemBudget) --S;
     return S;
 }
 
 static size_t slice_smem(int max_L, int S) {
     const int wpl = (max_L + 31) / 32;
-    return slice_smem_layout(max_L, wpl, max_L <= kGroupMaxL ? S : 1).total;
+    return max_L <= kGroupMaxL ? slice_smem_layout(max_L, wpl, S, true).total
+                               : slice_smem_layout(max_L, wpl, 1, false).total;
 }
 
 cudaError_t configure_slice(int max_L, int S) {
