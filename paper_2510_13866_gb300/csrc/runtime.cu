@@ -1,5 +1,6 @@
 // runtime.cu -- host side of the C ABI declared in include/hqmc.h: parameter validation,
 // FP64 tables, device layout, workspace, CUDA-graph capture of one sweep, read-outs.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -674,7 +675,14 @@ int stash_state(hqmc_ctx *c) {
     return HQMC_OK;
 }
 
+// NVTX range for the host-side enqueue of one phase (no-ops unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
+    NvtxRange sweep_range("hqmc sweep");
     const bool f64 = c->precision == HQMC_FP64;
     const int nk = int(c->classes.size());
     const bool prof = !capture && c->prof_max > 0 && c->prof_n < c->prof_max;
@@ -682,6 +690,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     if (prof) HQMC_CUDA(c, cudaEventRecord(pe[0], st));
     // permutation update at tau = beta before the FFBS of the sweep (Sec. 3.5.3)
     if (c->perm_on) {
+        NvtxRange r("hqmc permutations");
         int max_pairs = 0;
         for (auto &d : c->cdev) max_pairs = std::max(max_pairs, d.Nsig / 2);
         cudaError_t e = launch_perm(c->st, c->nchains, max_pairs, st);
@@ -704,6 +713,7 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     }
     (void)capture;
     for (int k = 0; k < nk; ++k) {
+        NvtxRange r("hqmc ffbs class");
         LClass &cl = c->classes[k];
         FfbsLaunch fl{};
         int *cls = reinterpret_cast<int *>(c->base + cl.cls_off);
@@ -746,7 +756,9 @@ int enqueue_sweep(hqmc_ctx *c, cudaStream_t st, bool capture) {
     int max_L = 0;
     for (auto &d : c->cdev) max_L = std::max(max_L, d.L);
     const int sgroup = slice_group(max_L, c->slices_per_cta, slice_work(c), c->num_sms);
+    nvtxRangePushA("hqmc gibbs+measure");
     cudaError_t e = launch_slice(c->st, c->nchains, max_M, max_L, sgroup, true, st);
+    nvtxRangePop();
     if (e != cudaSuccess) return cuda_fail(c, e, "slice launch");
     if (prof) {
         HQMC_CUDA(c, cudaEventRecord(pe[3], st));
