@@ -135,8 +135,8 @@ __device__ __forceinline__ void async_chunk(vec2_t<T> *sdst, int sc, const vec2_
 }
 
 // GAUSS: the class holds Gaussian-field chains (U < 0): their slice potentials are read from
-// the W arrays and their log-weight estimate tracks the interior concentration; the Hirsch-
-// only instantiation carries none of that code.
+// the W arrays and their log-weight estimate sums the concentration of every position along
+// the drawn path; the Hirsch-only instantiation carries none of that code.
 // STN: line convolutions by the periodic stencil (stencil_store) instead of the FFT.
 // BLK: the general work units -- FFBS blocks B < M and/or a permutation at tau = beta (the
 // closed-loop instantiation carries none of that bookkeeping).  With a permutation P the
@@ -458,9 +458,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) ffbs_kernel(DevSt
             if (!(fin0 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             if (has1 && !(fin1 > T(0))) atomicAdd(&st.meas[c].nonpositive, 1ull);
             const double inf = __longlong_as_double(0x7ff0000000000000LL);
-            // Hirsch units: len x the end concentration; Gaussian units: the concentrations
-            // at the drawn sites of positions 1 .. len-1 (kin, from the backward pass), plus
-            // the end's
+            // Hirsch units: len x the end concentration; Gaussian units: the conditional means
+            // of the concentration over positions 1 .. len-1 given the drawn next sites (kin,
+            // from the backward pass; calibration factor in FP64), plus the end's
             const double kap0 = double(top0) / double(fin0), kap1 = double(top1) / double(fin1);
             const double err0 = !(fin0 > T(0)) ? inf
                                 : (GAUSS && cd.gauss) ? logw_err_estimate<T>(gauss_sum_factor<T>() * kin0 + kap0, STN ? len : 1, L, STN)

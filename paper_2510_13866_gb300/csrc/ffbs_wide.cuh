@@ -419,8 +419,9 @@ __global__ void __launch_bounds__(WideGeo<T, L>::NT, WideGeo<T, L>::MINB) ffbs_w
             for (int k = 0; k < nwl; ++k) {
                 const T fin = endv[k], top = endv[WPC + k];
                 part[k] = double(ibuf[9 + k]) * ln2 + log(double(fin));
-                // Hirsch units: len x the end concentration; Gaussian units: the concentrations
-                // at the drawn sites of positions 1 .. len-1, plus the end's
+                // Hirsch units: len x the end concentration; Gaussian units: the conditional
+                // means of the concentration over positions 1 .. len-1 given the drawn next
+                // sites (calibration factor in FP64), plus the end's
                 const double kap = double(top) / double(fin);
                 err[k] = !(fin > T(0)) ? inf
                          : (GAUSS && cd.gauss) ? logw_err_estimate<T>(gauss_sum_factor<T>() * double(endv[3 * WPC + k]) + kap, 1, L, false)
