@@ -347,15 +347,20 @@ def observables(lat, shapes, sweeps, open_path=True):
 
 def kernel_source_digest(workload="L32"):
     """Digest of the sources the workload's FFBS kernels compile from (the register kernel for
-    L <= 32, the wide kernel too otherwise): the committed DRAM counters apply only to them."""
+    L <= 32, the wide kernel too otherwise), comments and whitespace left out: the committed
+    DRAM counters apply only to this code."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     files = ("ffbs.cuh", "device_common.cuh") if workload == "L32" else ("ffbs.cuh", "ffbs_wide.cuh",
                                                                           "device_common.cuh")
     for f in files:
-        with open(os.path.join(ROOT, "paper_2510_13866_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2510_13866_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
